@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the Aho-Corasick scan on GB300.
+
+Workload (default): 256 MiB of i.i.d. uniform DNA text (uint8) against
+10,000 distinct patterns of length U[16,64] (half cut from the text), one
+machine (K = 1), seeded synthetic data. A step is one pass of the whole hot
+path over the text: chunked scan with warm-up, match emission, per-pattern
+counts, sort of the matches and conversion to (position, id) records, with
+the text resident in HBM (it is larger than L2, so no flush is needed between
+steps). The machine is built once beforehand (host time reported apart).
+
+Metric: text GB/s (bytes of text scanned per second, the throughput of the
+paper's Eq. (1) with the machine already built). Also reported: the scan
+kernel against the HBM roofline, the same metric end to end through the C ABI
+with the text in pinned host memory (copy in, scan, results copied out), the
+other partitions of the same workload (K = 4/16/64 pattern subsets, 2-bit
+packed text), and the oracle on the host cores.
+
+``--impl reference`` times the oracle (plain C Aho-Corasick with failure
+links) on the host cores on bounded samples of the same workload.
+
+Multi-GPU (torchrun): every rank scans its own copy (replicas; the scan has
+no exchange step), the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "AC scan text GB/s"
+UNIT = "GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--subsets", type=int, default=1)
+    ap.add_argument("--fmt", default="u8", choices=["u8", "packed2"])
+    ap.add_argument("--mib", type=int, default=256, help="text size in MiB")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- peaks and clocks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+REASONS = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.gpu),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS[1:], parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle on the host cores
+def cpu_baseline(w, target_s: float = 1.5):
+    """The oracle (failure-link AC, unchanged) over text chunks on all host
+    cores, on a sample of the text sized for ~target_s of wall time."""
+    import oracle
+    cores = os.cpu_count() or 1
+    m = oracle.Machine(w.patterns)
+    probe = w.text[: min(w.text.size, 8 << 20)]
+    t0 = time.perf_counter()
+    m.scan_mt(probe, cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    nbytes = int(min(w.text.size, max(probe.size, probe.size * target_s / dt)))
+    sample = w.text[:nbytes]
+    t0 = time.perf_counter()
+    m.scan_mt(sample, cores)
+    dt = time.perf_counter() - t0
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nbytes / 2**20:.0f} MiB of the text, all {len(w.patterns)} patterns, "
+                      f"oracle (failure-link Aho-Corasick, C) over {cores} text chunks on {cores} threads",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    w = workloads.config2(n=args.mib << 20)
+    cores = os.cpu_count() or 1
+    m = oracle.Machine(w.patterns)
+    sample = min(w.text.size, 32 << 20)
+    for i in range(args.warmup):
+        m.scan_mt(w.text[:sample], cores)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        off = (i * sample) % max(1, w.text.size - sample + 1)
+        m.scan_mt(w.text[off:off + sample], cores)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w.name, "subsets": 1, "fmt": "u8", "text_bytes": int(w.text.size),
+                       "patterns": len(w.patterns)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample >> 20} MiB of the text per step, all patterns, {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1403_1305_gb300", "csrc", "scan.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_key: str):
+    """DRAM bytes per launch of the scan kernel from a committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "scan_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    e = d.get("per_launch", {}).get(workload_key)
+    return e.get("dram_bytes") if e else None
+
+
+def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
+    """Device-resident text: returns (total_s, scan_s_per_step, M)."""
+    P = a.num_patterns
+    d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_counts = torch.zeros(P, dtype=torch.int64, device="cuda")
+    # size the output from one untimed pass
+    probe_cap = 1 << 20
+    d_keys = torch.empty(probe_cap, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        A.ac_scan_keys_async(a, d_text, n, fmt, stream, d_keys, probe_cap, d_num, d_counts)
+    stream.synchronize()
+    M = int(d_num.item())
+    cap = 1 << max(10, int(np.ceil(np.log2(max(M, 1) * 1.25 + 1))))
+    d_keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+    d_m = torch.empty(cap, dtype=torch.int64, device="cuda")
+
+    def step(ev0=None, ev1=None):
+        if ev0 is not None:
+            ev0.record(stream)
+        A.ac_scan_keys_async(a, d_text, n, fmt, stream, d_keys, cap, d_num, d_counts)
+        if ev1 is not None:
+            ev1.record(stream)
+        A.ac_sort_keys_async(a, n, d_keys, d_num, cap, stream, d_m, d_num)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for i in range(steps):
+            step(*evs[i])
+        end.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    total = start.elapsed_time(end) / 1e3
+    scan = sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps / 1e3
+    M2 = int(d_num.item())
+    assert M2 == M, (M, M2)
+    return total, scan, M
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1403_1305_gb300 import ac as A
+
+    world, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    w = workloads.config2(n=args.mib << 20)
+    fmt = A.AC_U8 if args.fmt == "u8" else A.AC_PACKED2
+    host_text = w.text if fmt == A.AC_U8 else workloads.pack2(w.text)
+    n = int(w.text.size)
+    nbytes = int(host_text.size)
+    t0 = time.perf_counter()
+    a = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=args.subsets, device=dev)
+    build_s = time.perf_counter() - t0
+    st = A.ac_stats(a)
+    d_text = torch.from_numpy(host_text).to(f"cuda:{dev}")
+    stream = torch.cuda.Stream()
+
+    with ClockSampler(dev) as clk:
+        total, scan_s, M = time_device_path(A, torch, a, d_text, n, fmt, args.steps, args.warmup, pg, stream)
+    total = max_over_ranks(pg, total)
+    value = nbytes * world * args.steps / total / 1e9
+    clocks = clk.summary()
+
+    # roofline of the scan kernel: the text read once from HBM (bound), against
+    # K lookups per symbol at 32 shared-memory lookups per clock per SM
+    achieved = nbytes / scan_s / 1e9
+    lookups = args.subsets * n
+    lookup_rate_peak = n_sm * 32 * sm_mhz * 1e6
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    t_lookup = lookups / lookup_rate_peak
+    bound = "hbm" if t_hbm >= t_lookup else "smem_lookup"
+    key = f"{w.name}-K{args.subsets}-{args.fmt}"
+    roofline = {"bound": bound, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": ncu_traffic(key),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "scan_kernel (+ memsets, error mark)", "kernel_ms": scan_s * 1e3,
+                "algorithmic_bytes_per_launch": nbytes,
+                "roofline_ms": max(t_hbm, t_lookup) * 1e3,
+                "frac_of_roofline_time": max(t_hbm, t_lookup) / scan_s,
+                "lookup_peak_per_s": lookup_rate_peak, "lookups_per_launch": lookups}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w.name, "text_bytes": nbytes, "symbols": n, "fmt": args.fmt,
+                       "patterns": len(w.patterns), "pattern_len": [16, 64], "subsets": args.subsets,
+                       "states": st["states"], "table_bytes": st["table_bytes"], "smem_states": st["smem_states"],
+                       "matches": M, "build_ms": build_s * 1e3, "parallelism": f"replicas{world}",
+                       "l2": "text (256 MiB) larger than L2 (129 MB): no flush between steps",
+                       "scan_config": A.ac_get_scan_config(a)},
+            "roofline": roofline, "clocks": clocks,
+            "gpu_launches": 4 * args.steps,
+            "gpu_launches_note": "own kernels per step: scan, error mark, key pad, key->record convert "
+                                 "(plus the CUB radix-sort kernels compiled into the library)"}
+
+    if not args.no_e2e:
+        # end to end through the C ABI: pinned host text in, host results out
+        pinned = torch.from_numpy(host_text).pin_memory()
+        for _ in range(2):
+            A.ac_scan(a, pinned, n=n, fmt=fmt)
+        barrier(pg)
+        times = []
+        for _ in range(max(3, args.steps // 4)):
+            t0 = time.perf_counter()
+            m, c = A.ac_scan(a, pinned, n=n, fmt=fmt)
+            times.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(pg, statistics.median(times))
+        line["e2e"] = {"value": nbytes * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": int(m.shape[0] * 8 + c.size * 8 + 16),
+                       "api": "ac_scan(host pinned text) -> host matches + counts", "ms": e2e_s * 1e3}
+
+    if not args.no_variants:
+        var = {}
+        for K, f in ((4, "u8"), (16, "u8"), (64, "u8"), (1, "packed2"), (16, "packed2")):
+            if K == args.subsets and f == args.fmt:
+                continue
+            fm = A.AC_U8 if f == "u8" else A.AC_PACKED2
+            ht = w.text if fm == A.AC_U8 else workloads.pack2(w.text)
+            av = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=K, device=dev)
+            dt = torch.from_numpy(ht).to(f"cuda:{dev}")
+            tt, ss, mm = time_device_path(A, torch, av, dt, n, fm, max(3, args.steps // 4), 2, pg, stream)
+            steps_v = max(3, args.steps // 4)
+            var[f"K{K}-{f}"] = {"GBps": ht.size * steps_v / tt / 1e9, "symbols_per_s": n * steps_v / tt,
+                                "scan_ms": ss * 1e3, "matches": mm,
+                                "smem_states": A.ac_stats(av)["smem_states"], "states": A.ac_stats(av)["states"]}
+            del av, dt
+        line["variants"] = var
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

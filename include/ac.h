@@ -1,0 +1,283 @@
+/*
+ * ac.h — C ABI of libacgb300: exact multiple-pattern matching (Aho-Corasick)
+ * with the scan on an NVIDIA GB300 (sm_103a).
+ *
+ * Problem (paper, Abstract and Section I): locate every occurrence of a set
+ * of patterns in a text. The result of a scan is the set
+ *     M = { (e, j) : |P_j| <= e+1 <= n  and  text[e-|P_j|+1 .. e] = P_j }
+ * as ac_match records sorted by end position e (0-based, inclusive), then by
+ * pattern id j (the index of P_j in the array given to ac_build), and
+ * counts[j] = the number of records with pattern id j.
+ *
+ * The machine (Section II.A): goto function, failure function and output
+ * function, with failure transitions folded into regular ones (the "AC-opt"
+ * machine of Section III, reference [4]) so the scan does one table lookup
+ * per text symbol. Two partition axes (Section III): the text is cut into
+ * chunks, each warmed up on the (longest pattern - 1) symbols before it
+ * (input-focused split), and the pattern set can be cut into K subsets with
+ * one machine each, all scanning the same text (pattern-focused split, the
+ * paper's Fig. 5 approach).
+ *
+ * Conventions for every call:
+ *  - Return value: AC_OK (0) or a negative AC_E* code; on error no output is
+ *    produced (result structs are left zeroed) and ac_last_error() returns a
+ *    one-line description for the calling thread.
+ *  - Pointers marked "device" are CUDA device pointers on the automaton's
+ *    device; "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - Inputs are borrowed for the duration of the call only (asynchronous
+ *    calls: until the work queued on the stream has finished).
+ *  - Objects returned through ac_automaton**, ac_server** and ac_result are
+ *    owned by the library; release them with ac_free, ac_serve_destroy and
+ *    ac_result_free.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).
+ *  - One automaton may be used by several threads and streams at once; scans
+ *    do not modify it (ac_tune and ac_set_scan_config do, and must not race
+ *    with scans of the same automaton).
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AC_API __attribute__((visibility("default")))
+#else
+#define AC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define AC_OK 0
+#define AC_EINVAL (-1)    /* bad argument: NULL, P = 0, empty pattern, byte outside the alphabet, bad fmt */
+#define AC_ENOMEM (-2)    /* host or device allocation failed */
+#define AC_ERANGE (-3)    /* size limit: n >= 2^32, too many states, output beyond capacity after a retry */
+#define AC_ECUDA (-4)     /* a CUDA call failed (no device, launch error, ...) */
+#define AC_ETIMEDOUT (-5) /* a bounded device-side wait ran out, or ac_serve_wait timed out */
+#define AC_EAGAIN (-6)    /* result not ready yet (ac_serve_poll) */
+#define AC_EBUSY (-7)     /* server queue full (non-blocking submit refused) */
+
+/* ------------------------------------------------------------ enums */
+#define AC_U8 0      /* one byte per symbol */
+#define AC_PACKED2 1 /* 2-bit codes, 4 symbols per byte; symbol i at bits 2*(i%4) of byte i/4;
+                        code k stands for the k-th letter of a 4-letter alphabet */
+
+#define AC_HOST 0
+#define AC_DEVICE 1
+
+#define AC_PLACE_AUTO 0   /* pick per subset: whole table in shared memory if it fits, else hybrid */
+#define AC_PLACE_SMEM 1   /* whole table in shared memory; AC_ERANGE at build if it does not fit */
+#define AC_PLACE_HYBRID 2 /* the first (breadth-first) states in shared memory, the rest read through L2 */
+#define AC_PLACE_GLOBAL 3 /* every lookup through L2 / HBM */
+
+/* ------------------------------------------------------------ types */
+typedef struct ac_automaton ac_automaton;
+typedef struct ac_server ac_server;
+
+typedef struct {
+    uint32_t pos;        /* 0-based end position (inclusive) of the occurrence */
+    uint32_t pattern_id; /* index of the pattern in the array given to ac_build */
+} ac_match;
+
+typedef struct {
+    const char *alphabet;  /* NUL-terminated string of distinct bytes forming the alphabet (order = symbol
+                              codes, e.g. "ACGT"), or NULL: the distinct bytes of the patterns, ascending.
+                              Text bytes outside it send the machine to the root state. */
+    uint32_t num_subsets;  /* K >= 1 pattern-subset machines over contiguous id ranges of ceil(P/K);
+                              0 means 1; K > P is AC_EINVAL */
+    int32_t placement;     /* AC_PLACE_* */
+    int32_t device;        /* CUDA device ordinal; -1 builds on the host only (inspection, no scans) */
+    uint32_t smem_table_bytes; /* cap on table bytes held in shared memory per CTA; 0 = as much as fits */
+} ac_build_opts;
+
+typedef struct {
+    ac_match *matches;     /* host array of num_matches records, sorted; library-owned */
+    uint64_t num_matches;
+    uint64_t *counts;      /* host array of num_patterns counts; library-owned */
+    uint32_t num_patterns;
+} ac_result;
+
+typedef struct {
+    uint32_t num_patterns;
+    uint32_t num_subsets;
+    uint32_t sigma;          /* alphabet size */
+    uint32_t max_len;        /* longest pattern */
+    uint64_t states;         /* sum over subsets */
+    uint64_t table_bytes;    /* sum over subsets of the dense goto tables */
+    uint64_t output_entries; /* sum over states of |output(state)| */
+    uint64_t smem_states;    /* sum over subsets of the states held in shared memory */
+    double build_ms;         /* host time of trie + failure + fold + renumber (all subsets) */
+    double upload_ms;        /* host->device copy of the tables */
+    int32_t device;
+    uint32_t row_len;        /* current scan configuration (symbols per chain) */
+    uint32_t threads;
+    uint32_t chains;
+} ac_stats_t;
+
+/* Read-only host view of one subset machine (valid until ac_free). States are
+ * numbered breadth-first (root 0). table[s*sigma + c] = next state of s on
+ * symbol c, with bit 31 set when the next state's output is not empty.
+ * out_ids[out_off[s] .. out_off[s+1]) = output(s), ascending global ids. */
+typedef struct {
+    uint32_t id_lo, id_hi;   /* pattern ids [id_lo, id_hi) of this subset */
+    uint32_t max_len;        /* longest pattern of the subset */
+    uint32_t sigma;
+    uint32_t states;
+    uint32_t smem_states;    /* states whose rows the scan keeps in shared memory */
+    const uint32_t *table;   /* states x sigma */
+    const uint32_t *fail;    /* states (failure function, breadth-first ids) */
+    const uint32_t *depth;   /* states */
+    const uint32_t *out_off; /* states + 1 */
+    const uint32_t *out_ids;
+    const uint8_t *symbol_of_byte; /* 256 entries; sigma = outside the alphabet */
+} ac_subset_view;
+
+/* Scan configuration (ac_set_scan_config / ac_tune). Zero fields = defaults. */
+typedef struct {
+    uint32_t row_len; /* text symbols per chain (rounded to the stage size) */
+    uint32_t threads; /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t chains;  /* independent chains per thread: 1, 2 or 4 */
+    uint32_t ctas;    /* persistent grid size; 0 = one per SM */
+} ac_scan_config;
+
+/* ------------------------------------------------------------ automaton */
+
+/* Build the machines for patterns pats[0..P) (lengths lens[]), Section II.A
+ * steps: goto function by inserting the patterns in order, failure function
+ * breadth-first with output merge, failure transitions folded into a dense
+ * table, states renumbered breadth-first; then (device >= 0) the tables are
+ * copied to the device. Patterns are copied; the caller keeps ownership.
+ * Errors: AC_EINVAL (pats/lens/out NULL, P = 0, an empty pattern, a byte
+ * outside opts->alphabet, K > P), AC_ERANGE (>= 2^31 states in a subset, or
+ * AC_PLACE_SMEM and a table that does not fit), AC_ENOMEM, AC_ECUDA. */
+AC_API int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
+             const ac_build_opts *opts, ac_automaton **out);
+
+/* Release an automaton (NULL is a no-op). */
+AC_API void ac_free(ac_automaton *a);
+
+AC_API int ac_stats(const ac_automaton *a, ac_stats_t *out);
+
+/* Host view of subset k (0 <= k < K). */
+AC_API int ac_subset(const ac_automaton *a, uint32_t k, ac_subset_view *out);
+
+/* Set or read the scan configuration used by later scans of `a`. */
+AC_API int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg);
+AC_API int ac_get_scan_config(const ac_automaton *a, ac_scan_config *cfg);
+
+/* Autotune: time candidate configurations on a text of n symbols (device
+ * pointer d_text, format fmt) on `stream`, keep the fastest in `a` and
+ * return it in *chosen (may be NULL). */
+AC_API int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+            ac_scan_config *chosen);
+
+/* ------------------------------------------------------------ scans */
+
+/* Scan n symbols of `text` (fmt AC_U8 or AC_PACKED2; mem AC_HOST or
+ * AC_DEVICE) and return the sorted matches and the counts in *out (host
+ * arrays, release with ac_result_free). Synchronous: returns when the result
+ * is on the host. Host text is copied to the device inside the call. */
+AC_API int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int mem,
+            void *stream, ac_result *out);
+
+/* Asynchronous scan, device in and device out, no host synchronisation:
+ * queues the work on `stream` and returns. d_matches has room for `cap`
+ * records; *d_num_matches (device, uint64) receives the true number of
+ * matches M; when M > cap the records are unspecified (retry with cap >= M).
+ * *d_num_matches == UINT64_MAX means a device-side wait ran out (error).
+ * d_counts (device, num_patterns uint64) may be NULL. Scratch memory comes
+ * from the library's stream-ordered pool. */
+AC_API int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                  ac_match *d_matches, uint64_t cap, uint64_t *d_num_matches, uint64_t *d_counts);
+
+/* The two stages of ac_scan_async, for callers that time or overlap them.
+ * ac_scan_keys_async: steps of the scan up to the unsorted matches — every
+ * match as one uint64 key (pos << ac_key_shift(a)) | pattern_id in d_keys
+ * (room for cap keys; order unspecified), the true count M in *d_num (device
+ * uint64; UINT64_MAX if a device-side wait ran out) and, if d_counts is not
+ * NULL, the per-pattern counts (device, num_patterns uint64, zeroed by the
+ * call). Keys beyond cap are dropped (M still counts them). */
+AC_API int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                              uint64_t *d_keys, uint64_t cap, uint64_t *d_num, uint64_t *d_counts);
+/* Bits below the position in a key: ceil(log2(num_patterns)), at least 1. */
+AC_API int ac_key_shift(const ac_automaton *a);
+/* Sort the first min(*d_num, cap) keys of d_keys (device; cap entries, the
+ * entries at and beyond *d_num are overwritten) ascending and write them as
+ * ac_match records to d_matches (device, cap records); *d_num_out (device,
+ * may alias d_num) receives *d_num. n = the text length the keys came from
+ * (bounds the sort's key bits). Scratch comes from the library's pool. */
+AC_API int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num,
+                              uint64_t cap, void *stream, ac_match *d_matches, uint64_t *d_num_out);
+
+/* One text of a batch. */
+typedef struct {
+    uint32_t automaton; /* index into the automata array */
+    int32_t fmt;        /* AC_U8 or AC_PACKED2 */
+    const uint8_t *text;
+    uint64_t n;         /* symbols */
+} ac_batch_item;
+
+/* Scan ni texts, each against one of na resident automata, in one persistent
+ * launch (replayed from a CUDA graph when the same batch shape recurs).
+ * mem = AC_HOST or AC_DEVICE for all item texts. outs[i] receives item i's
+ * result (counts sized by its automaton's pattern count). Synchronous. */
+AC_API int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const ac_batch_item *items,
+                  uint32_t ni, int mem, void *stream, ac_result *outs);
+
+/* Release the arrays of a result (NULL or zeroed is a no-op). */
+AC_API void ac_result_free(ac_result *r);
+
+/* ------------------------------------------------------------ serving */
+typedef struct {
+    uint64_t device_mem_budget; /* bytes of device memory the server may hold for texts and results
+                                   (0 = 4 GiB) */
+    uint32_t max_batch_items;   /* most requests coalesced into one launch (0 = 256) */
+    uint32_t max_queue;         /* queued requests before submit refuses with AC_EBUSY (0 = 65536) */
+    uint32_t num_streams;       /* launches in flight at once (0 = 2) */
+    uint32_t max_wait_us;       /* how long the scheduler lets a partial batch wait for more arrivals
+                                   (0 = none) */
+} ac_serve_opts;
+
+/* Start a server over na resident automata (borrowed; they must outlive the
+ * server). A scheduler thread admits requests by memory, coalesces them into
+ * batched launches and completes them. */
+AC_API int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_opts *opts,
+                    ac_server **out);
+
+/* Queue a request: scan host text[0..n) (copied before returning) with
+ * automaton `automaton`. *ticket identifies it. AC_EBUSY when the queue is
+ * full, AC_ERANGE when the text alone exceeds the memory budget. */
+AC_API int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt,
+                    uint64_t *ticket);
+
+/* Non-blocking: AC_EAGAIN while pending; AC_OK moves the result into *out
+ * (the ticket is then consumed). */
+AC_API int ac_serve_poll(ac_server *s, uint64_t ticket, ac_result *out);
+
+/* Blocking with a timeout in milliseconds: AC_ETIMEDOUT if not done in time. */
+AC_API int ac_serve_wait(ac_server *s, uint64_t ticket, uint32_t timeout_ms, ac_result *out);
+
+typedef struct {
+    uint64_t submitted, completed, launches, items_launched, queued, in_flight;
+    double p50_ms, p99_ms, mean_batch_items;
+} ac_serve_stats_t;
+
+AC_API int ac_serve_stats(ac_server *s, ac_serve_stats_t *out);
+
+/* Stop the scheduler (pending requests complete first) and release everything. */
+AC_API void ac_serve_destroy(ac_server *s);
+
+/* ------------------------------------------------------------ misc */
+AC_API const char *ac_strerror(int code);
+AC_API const char *ac_last_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+AC_API int ac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AC_H */

@@ -1,0 +1,112 @@
+// Internal declarations shared by the translation units of libacgb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ac.h"
+
+namespace acgb {
+
+constexpr uint32_t kFlag = 0x80000000u;  // table entry bit: next state has a non-empty output
+constexpr uint32_t kStateMask = 0x7fffffffu;
+
+// ---------------------------------------------------------------- host machine
+struct HostSubset {
+    uint32_t id_lo = 0, id_hi = 0;  // global pattern ids [id_lo, id_hi)
+    uint32_t max_len = 0;
+    uint32_t states = 0;
+    std::vector<uint32_t> table;    // states * sigma, breadth-first ids | kFlag
+    std::vector<uint32_t> fail;     // breadth-first ids
+    std::vector<uint32_t> depth;
+    std::vector<uint32_t> out_off;  // states + 1
+    std::vector<uint32_t> out_ids;  // global ids, ascending per state
+};
+
+// Device descriptor of one subset machine (array in device memory, one per subset).
+struct SubsetDev {
+    const uint32_t *table;    // states * sigma
+    const uint32_t *out_off;  // states + 1
+    const uint32_t *out_ids;
+    uint32_t states;
+    uint32_t smem_states;     // rows [0, smem_states) are staged into shared memory
+    uint32_t warm;            // max_len - 1: symbols of warm-up a chain needs
+    uint32_t id_lo;
+};
+
+struct DeviceSubset {
+    uint32_t *table = nullptr, *out_off = nullptr, *out_ids = nullptr;
+};
+
+}  // namespace acgb
+
+struct ac_automaton {
+    uint32_t P = 0, K = 1, sigma = 0, max_len = 0;
+    uint8_t sym_of_byte[256];   // sigma = outside the alphabet
+    uint8_t byte_of_sym[256];
+    bool dna_acgt = false;      // alphabet is exactly "ACGT" in this order
+    int32_t placement = AC_PLACE_AUTO;
+    int32_t device = -1;
+    uint32_t smem_cap_bytes = 0;
+    std::vector<acgb::HostSubset> subs;
+    // device side
+    std::vector<acgb::DeviceSubset> dsubs;
+    acgb::SubsetDev *d_desc = nullptr;   // K descriptors
+    std::vector<acgb::SubsetDev> h_desc; // host copy of the descriptors
+    uint32_t table_smem_bytes = 0;       // bytes of table staged in shared memory per CTA (max over subsets)
+    ac_scan_config cfg{};
+    double build_ms = 0, upload_ms = 0;
+};
+
+namespace acgb {
+
+// build.cpp
+int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
+                   ac_automaton *a);
+
+// error reporting (capi.cu)
+int set_error(int code, const char *fmt, ...);
+
+// scan.cu
+struct ScanText {
+    const uint8_t *d_text;  // 16-byte aligned device pointer
+    uint64_t n;             // symbols
+    int fmt;
+};
+
+struct ScanOut {
+    unsigned long long *keys;   // (pos << 32 | id), capacity `cap`
+    uint64_t cap;
+    unsigned long long *num;    // match counter (device)
+    unsigned long long *counts; // per-pattern counts (device) or null
+    uint32_t *err;              // device error word
+};
+
+// Stage geometry shared by host planning and the kernels.
+constexpr uint32_t kStageBytes = 32;   // bytes of one chain's text per pipeline stage
+
+int scan_smem_limit(int device);
+uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
+void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
+int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
+                cudaStream_t stream);
+int launch_fill_u64(unsigned long long *p, uint64_t count, unsigned long long value, cudaStream_t stream);
+int launch_keys_to_matches(const unsigned long long *keys, const unsigned long long *num, uint64_t cap,
+                           uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
+                           cudaStream_t stream);
+int key_shift_for(const ac_automaton *a);
+int launch_pad_keys(unsigned long long *keys, const unsigned long long *num, uint64_t cap, cudaStream_t stream);
+int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t stream);
+int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int end_bit,
+              void *temp, size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted);
+
+// memory (capi.cu)
+void *dev_alloc(size_t bytes, cudaStream_t stream);
+void dev_free(void *p, cudaStream_t stream);
+
+}  // namespace acgb

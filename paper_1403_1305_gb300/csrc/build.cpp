@@ -1,0 +1,227 @@
+// Host construction of the matching machines (run once per pattern set).
+//
+// Steps, per pattern subset (Section II.A, Fig. 1; the folded table is the
+// "AC-opt" machine of Section III / reference [4]):
+//   1. goto function: insert the subset's patterns in their order, numbering
+//      new states consecutively from root 0;
+//   2. failure function breadth-first, folding each missing transition into
+//      the transition of the failure state (so the table holds the complete
+//      next-state function), and merging each state's output with the output
+//      of its failure state;
+//   3. states renumbered in breadth-first order so the shallow states, where
+//      a walk over random text spends most of its time, form a prefix of the
+//      table that the scan keeps in shared memory.
+// Subsets (Section III's pattern-focused split, the paper's Fig. 5) are
+// contiguous id ranges of as-equal-as-possible size, built on host threads.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+
+#include "ac_internal.h"
+
+namespace acgb {
+
+namespace {
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+int build_subset(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, uint32_t hi,
+                 const uint8_t *sym, uint32_t sigma, HostSubset &S, std::string &why) {
+    S.id_lo = lo;
+    S.id_hi = hi;
+    // 1. goto function (trie) with consecutive state numbers
+    std::vector<uint32_t> child(sigma, kNone);
+    std::vector<uint32_t> depth(1, 0);
+    std::vector<std::pair<uint32_t, uint32_t>> finals;  // (state, pattern id)
+    finals.reserve(hi - lo);
+    uint64_t ns = 1;
+    for (uint32_t j = lo; j < hi; ++j) {
+        uint32_t s = 0;
+        S.max_len = std::max(S.max_len, lens[j]);
+        for (uint32_t k = 0; k < lens[j]; ++k) {
+            uint32_t c = sym[pats[j][k]];
+            uint64_t idx = (uint64_t)s * sigma + c;
+            uint32_t t = child[idx];
+            if (t == kNone) {
+                if (ns >= (uint64_t)kStateMask) {
+                    why = "more than 2^31-1 states in one subset";
+                    return AC_ERANGE;
+                }
+                t = (uint32_t)ns++;
+                child[idx] = t;
+                child.resize(ns * sigma, kNone);
+                depth.push_back(depth[s] + 1);
+            }
+            s = t;
+        }
+        finals.emplace_back(s, j);
+    }
+    const uint32_t N = (uint32_t)ns;
+
+    // 2. breadth-first failure function with the missing transitions folded in
+    std::vector<uint32_t> order;
+    order.reserve(N);
+    std::vector<uint32_t> fail(N, 0);
+    order.push_back(0);
+    for (uint32_t c = 0; c < sigma; ++c) {
+        uint32_t t = child[c];
+        if (t == kNone) {
+            child[c] = 0;  // the root loops on symbols that start no pattern
+        } else {
+            fail[t] = 0;
+            order.push_back(t);
+        }
+    }
+    for (size_t h = 1; h < order.size(); ++h) {
+        uint32_t r = order[h];
+        uint64_t fr = (uint64_t)fail[r] * sigma, rr = (uint64_t)r * sigma;
+        for (uint32_t c = 0; c < sigma; ++c) {
+            uint32_t t = child[rr + c];
+            if (t == kNone) {
+                child[rr + c] = child[fr + c];
+            } else {
+                fail[t] = child[fr + c];
+                order.push_back(t);
+            }
+        }
+    }
+
+    // breadth-first rank of every state
+    std::vector<uint32_t> rank(N);
+    for (uint32_t i = 0; i < N; ++i) rank[order[i]] = i;
+
+    // output function: own patterns merged with the output of the failure state
+    std::stable_sort(finals.begin(), finals.end(),
+                     [](const std::pair<uint32_t, uint32_t> &x, const std::pair<uint32_t, uint32_t> &y) {
+                         return x.first < y.first;
+                     });
+    std::vector<uint32_t> own_off(N + 1, 0);
+    for (auto &f : finals) own_off[f.first + 1]++;
+    for (uint32_t i = 0; i < N; ++i) own_off[i + 1] += own_off[i];
+    S.out_off.assign(N + 1, 0);
+    S.out_ids.clear();
+    for (uint32_t i = 0; i < N; ++i) {
+        uint32_t t = order[i];
+        const uint32_t *own_b = nullptr;
+        size_t n_own = own_off[t + 1] - own_off[t];
+        std::vector<uint32_t> own(n_own);
+        for (size_t q = 0; q < n_own; ++q) own[q] = finals[own_off[t] + q].second;
+        size_t start = S.out_ids.size();
+        if (i > 0) {
+            uint32_t fr = rank[fail[t]];  // fail[t] comes earlier in breadth-first order
+            size_t fb = S.out_off[fr], fe = S.out_off[fr + 1];
+            S.out_ids.resize(start + n_own + (fe - fb));
+            std::merge(own.begin(), own.end(), S.out_ids.begin() + fb, S.out_ids.begin() + fe,
+                       S.out_ids.begin() + start);
+        } else {
+            S.out_ids.insert(S.out_ids.end(), own.begin(), own.end());
+        }
+        (void)own_b;
+        if (S.out_ids.size() > 0xffffffffull) {
+            why = "output function larger than 2^32 entries";
+            return AC_ERANGE;
+        }
+        S.out_off[i + 1] = (uint32_t)S.out_ids.size();
+    }
+
+    // 3. renumbered dense table, with the output flag on each entry
+    S.states = N;
+    S.table.resize((size_t)N * sigma);
+    S.fail.resize(N);
+    S.depth.resize(N);
+    for (uint32_t i = 0; i < N; ++i) {
+        uint32_t s = order[i];
+        S.fail[i] = rank[fail[s]];
+        S.depth[i] = depth[s];
+        uint64_t rr = (uint64_t)s * sigma;
+        uint32_t *dst = &S.table[(size_t)i * sigma];
+        for (uint32_t c = 0; c < sigma; ++c) {
+            uint32_t nx = rank[child[rr + c]];
+            uint32_t flag = (S.out_off[nx + 1] > S.out_off[nx]) ? kFlag : 0u;
+            dst[c] = nx | flag;
+        }
+    }
+    return AC_OK;
+}
+
+}  // namespace
+
+int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
+                   ac_automaton *a) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!pats || !lens || P == 0) return set_error(AC_EINVAL, "ac_build: no patterns");
+    for (uint32_t j = 0; j < P; ++j)
+        if (lens[j] == 0 || !pats[j]) return set_error(AC_EINVAL, "ac_build: pattern %u is empty", j);
+
+    // symbol map (a1): byte -> symbol, sigma = outside the alphabet
+    memset(a->sym_of_byte, 0, sizeof(a->sym_of_byte));
+    memset(a->byte_of_sym, 0, sizeof(a->byte_of_sym));
+    bool used[256] = {false};
+    uint32_t sigma = 0;
+    if (opts && opts->alphabet) {
+        const unsigned char *al = (const unsigned char *)opts->alphabet;
+        for (size_t i = 0; al[i]; ++i) {
+            if (used[al[i]]) return set_error(AC_EINVAL, "ac_build: alphabet repeats byte 0x%02x", al[i]);
+            used[al[i]] = true;
+            a->byte_of_sym[sigma++] = al[i];
+        }
+        if (sigma == 0) return set_error(AC_EINVAL, "ac_build: empty alphabet");
+    } else {
+        for (uint32_t j = 0; j < P; ++j)
+            for (uint32_t k = 0; k < lens[j]; ++k) used[pats[j][k]] = true;
+        for (int b = 0; b < 256; ++b)
+            if (used[b]) a->byte_of_sym[sigma++] = (uint8_t)b;
+    }
+    if (sigma >= 256) return set_error(AC_ERANGE, "ac_build: alphabets of 256 symbols are not supported");
+    for (int b = 0; b < 256; ++b) a->sym_of_byte[b] = (uint8_t)sigma;
+    for (uint32_t s = 0; s < sigma; ++s) a->sym_of_byte[a->byte_of_sym[s]] = (uint8_t)s;
+    for (uint32_t j = 0; j < P; ++j)
+        for (uint32_t k = 0; k < lens[j]; ++k)
+            if (a->sym_of_byte[pats[j][k]] == sigma)
+                return set_error(AC_EINVAL, "ac_build: pattern %u holds byte 0x%02x outside the alphabet", j,
+                                 pats[j][k]);
+    a->sigma = sigma;
+    a->dna_acgt = sigma == 4 && a->byte_of_sym[0] == 'A' && a->byte_of_sym[1] == 'C' &&
+                  a->byte_of_sym[2] == 'G' && a->byte_of_sym[3] == 'T';
+    a->P = P;
+    a->max_len = 0;
+    for (uint32_t j = 0; j < P; ++j) a->max_len = std::max(a->max_len, lens[j]);
+
+    // subsets (a5)
+    uint32_t K = (opts && opts->num_subsets) ? opts->num_subsets : 1;
+    if (K > P) return set_error(AC_EINVAL, "ac_build: %u subsets for %u patterns", K, P);
+    a->K = K;
+    a->subs.assign(K, HostSubset());
+    std::vector<int> rc(K, AC_OK);
+    std::vector<std::string> why(K);
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    unsigned nthr = std::min<unsigned>(K, hw);
+    std::atomic<uint32_t> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            uint32_t k = next.fetch_add(1);
+            if (k >= K) break;
+            uint32_t lo = (uint32_t)((uint64_t)k * P / K), hi = (uint32_t)((uint64_t)(k + 1) * P / K);
+            try {
+                rc[k] = build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
+            } catch (const std::bad_alloc &) {
+                rc[k] = AC_ENOMEM;
+                why[k] = "host allocation failed";
+            }
+        }
+    };
+    if (nthr <= 1) {
+        worker();
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned i = 0; i < nthr; ++i) th.emplace_back(worker);
+        for (auto &t : th) t.join();
+    }
+    for (uint32_t k = 0; k < K; ++k)
+        if (rc[k] != AC_OK) return set_error(rc[k], "ac_build: subset %u: %s", k, why[k].c_str());
+    a->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return AC_OK;
+}
+
+}  // namespace acgb

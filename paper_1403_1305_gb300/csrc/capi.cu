@@ -1,0 +1,526 @@
+// C ABI entry points of libacgb300 (declared in include/ac.h): automaton
+// lifecycle, synchronous and asynchronous scans, results, errors.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <chrono>
+
+#include "ac_internal.h"
+
+namespace acgb {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_last_error[512] = "";
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(AC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return set_error(AC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ------------------------------------------------------------------ device memory
+// Scratch comes from one stream-ordered pool per device that keeps freed
+// memory reserved (release threshold = max), so steady-state scans allocate
+// without a device synchronisation.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaMemPool_t pool_for(int device) {
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pools[device] = p;
+    }
+    return g_pools[device];
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t stream) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t p = pool_for(dev);
+    void *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = p ? cudaMallocFromPoolAsync(&ptr, bytes, p, stream) : cudaMallocAsync(&ptr, bytes, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ptr;
+}
+
+void dev_free(void *p, cudaStream_t stream) {
+    if (p) cudaFreeAsync(p, stream);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            ok = false;
+            cudaGetLastError();
+            return;
+        }
+        if (prev != d && cudaSetDevice(d) != cudaSuccess) {
+            ok = false;
+            cudaGetLastError();
+        }
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Scratch allocations released (stream-ordered) when the scope ends.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    void *get(size_t bytes) {
+        void *p = dev_alloc(bytes, s);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    void release(void *p) {
+        for (auto &q : ptrs)
+            if (q == p) {
+                dev_free(q, s);
+                q = nullptr;
+            }
+    }
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(p, s);
+    }
+};
+
+static void free_device(ac_automaton *a) {
+    if (a->device < 0) return;
+    DeviceGuard g(a->device);
+    for (auto &d : a->dsubs) {
+        cudaFree(d.table);
+        cudaFree(d.out_off);
+        cudaFree(d.out_ids);
+    }
+    a->dsubs.clear();
+    if (a->d_desc) cudaFree(a->d_desc);
+    a->d_desc = nullptr;
+}
+
+static int upload(ac_automaton *a) {
+    auto t0 = std::chrono::steady_clock::now();
+    DeviceGuard g(a->device);
+    if (!g.ok) return set_error(AC_ECUDA, "ac_build: cannot use device %d", a->device);
+    a->dsubs.assign(a->K, DeviceSubset());
+    a->h_desc.assign(a->K, SubsetDev());
+    for (uint32_t k = 0; k < a->K; ++k) {
+        const HostSubset &h = a->subs[k];
+        DeviceSubset &d = a->dsubs[k];
+        size_t tb = h.table.size() * 4, ob = h.out_off.size() * 4, ib = std::max<size_t>(4, h.out_ids.size() * 4);
+        CK(cudaMalloc(&d.table, tb), "ac_build: table");
+        CK(cudaMalloc(&d.out_off, ob), "ac_build: output offsets");
+        CK(cudaMalloc(&d.out_ids, ib), "ac_build: output ids");
+        CK(cudaMemcpy(d.table, h.table.data(), tb, cudaMemcpyHostToDevice), "ac_build: copy");
+        CK(cudaMemcpy(d.out_off, h.out_off.data(), ob, cudaMemcpyHostToDevice), "ac_build: copy");
+        if (!h.out_ids.empty())
+            CK(cudaMemcpy(d.out_ids, h.out_ids.data(), h.out_ids.size() * 4, cudaMemcpyHostToDevice),
+               "ac_build: copy");
+        SubsetDev &s = a->h_desc[k];
+        s.table = d.table;
+        s.out_off = d.out_off;
+        s.out_ids = d.out_ids;
+        s.states = h.states;
+        s.smem_states = 0;
+        s.warm = h.max_len ? h.max_len - 1 : 0;
+        s.id_lo = h.id_lo;
+    }
+    CK(cudaMalloc(&a->d_desc, sizeof(SubsetDev) * a->K), "ac_build: descriptors");
+    CK(cudaMemcpy(a->d_desc, a->h_desc.data(), sizeof(SubsetDev) * a->K, cudaMemcpyHostToDevice),
+       "ac_build: descriptors");
+    a->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return AC_OK;
+}
+
+static uint32_t bits_for(uint64_t x) {
+    uint32_t b = 1;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
+static int check_scan_args(const ac_automaton *a, uint64_t n, int fmt) {
+    if (!a) return set_error(AC_EINVAL, "scan: automaton is NULL");
+    if (a->device < 0) return set_error(AC_EINVAL, "scan: automaton was built for the host only");
+    if (fmt != AC_U8 && fmt != AC_PACKED2) return set_error(AC_EINVAL, "scan: unknown text format %d", fmt);
+    if (fmt == AC_PACKED2 && a->sigma != 4)
+        return set_error(AC_EINVAL, "scan: 2-bit packed text needs a 4-letter alphabet (have %u)", a->sigma);
+    if (n >= (1ull << 32)) return set_error(AC_ERANGE, "scan: n = %llu symbols, the limit is 2^32-1",
+                                            (unsigned long long)n);
+    return AC_OK;
+}
+
+static uint64_t text_bytes(uint64_t n, int fmt) { return fmt == AC_U8 ? n : (n + 3) / 4; }
+
+// Device copy of the text at a 16-byte aligned address.
+static int stage_text(const uint8_t *text, uint64_t nbytes, int mem, cudaStream_t s, Scratch &sc,
+                      const uint8_t **d_text) {
+    if (mem == AC_DEVICE && ((uintptr_t)text & 15) == 0) {
+        *d_text = text;
+        return AC_OK;
+    }
+    uint8_t *buf = (uint8_t *)sc.get((nbytes + 15) & ~15ull);
+    if (!buf) return set_error(AC_ENOMEM, "scan: device text buffer of %llu bytes", (unsigned long long)nbytes);
+    CK(cudaMemcpyAsync(buf, text, nbytes, mem == AC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s),
+       "scan: text copy");
+    *d_text = buf;
+    return AC_OK;
+}
+
+}  // namespace acgb
+
+using namespace acgb;
+
+// ====================================================================== C ABI
+extern "C" {
+
+int ac_version(void) { return 10000; }
+
+const char *ac_strerror(int code) {
+    switch (code) {
+        case AC_OK: return "ok";
+        case AC_EINVAL: return "invalid argument";
+        case AC_ENOMEM: return "out of memory";
+        case AC_ERANGE: return "size out of range";
+        case AC_ECUDA: return "CUDA error";
+        case AC_ETIMEDOUT: return "timed out";
+        case AC_EAGAIN: return "not ready";
+        case AC_EBUSY: return "busy";
+        default: return "unknown error";
+    }
+}
+
+const char *ac_last_error(void) { return g_last_error; }
+
+int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
+             ac_automaton **out) {
+    if (!out) return set_error(AC_EINVAL, "ac_build: out is NULL");
+    *out = nullptr;
+    ac_automaton *a = nullptr;
+    try {
+        a = new ac_automaton();
+    } catch (...) {
+        return set_error(AC_ENOMEM, "ac_build: host allocation");
+    }
+    a->placement = opts ? opts->placement : AC_PLACE_AUTO;
+    a->device = opts ? opts->device : 0;
+    a->smem_cap_bytes = opts ? opts->smem_table_bytes : 0;
+    if (a->placement < AC_PLACE_AUTO || a->placement > AC_PLACE_GLOBAL) {
+        delete a;
+        return set_error(AC_EINVAL, "ac_build: unknown placement %d", a->placement);
+    }
+    int rc;
+    try {
+        rc = build_machines(pats, lens, P, opts, a);
+    } catch (const std::bad_alloc &) {
+        rc = set_error(AC_ENOMEM, "ac_build: host allocation");
+    }
+    if (rc == AC_OK && a->sigma == 4)
+        for (auto &s : a->subs)
+            if (s.states >= (1u << 30)) rc = set_error(AC_ERANGE, "ac_build: 2^30 states or more");
+    if (rc == AC_OK && a->device >= 0) {
+        rc = upload(a);
+        if (rc == AC_OK && a->placement == AC_PLACE_SMEM) {
+            ac_scan_config c{};
+            default_config(a, 1, AC_U8, &c);
+            int limit = scan_smem_limit(a->device);
+            uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
+            if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
+            for (auto &s : a->subs)
+                if ((uint64_t)s.states * 4 * a->sigma > avail)
+                    rc = set_error(AC_ERANGE, "ac_build: placement SMEM, but a table of %u states does not fit",
+                                   s.states);
+        }
+    }
+    if (rc != AC_OK) {
+        free_device(a);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return AC_OK;
+}
+
+void ac_free(ac_automaton *a) {
+    if (!a) return;
+    free_device(a);
+    delete a;
+}
+
+int ac_stats(const ac_automaton *a, ac_stats_t *o) {
+    if (!a || !o) return set_error(AC_EINVAL, "ac_stats: NULL argument");
+    memset(o, 0, sizeof(*o));
+    o->num_patterns = a->P;
+    o->num_subsets = a->K;
+    o->sigma = a->sigma;
+    o->max_len = a->max_len;
+    uint32_t rows_fit = 0;
+    if (a->device >= 0) {
+        ac_scan_config c{};
+        default_config(a, 1, AC_U8, &c);
+        int limit = scan_smem_limit(a->device);
+        uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
+        if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
+        rows_fit = a->placement == AC_PLACE_GLOBAL ? 0 : (uint32_t)(avail / (4ull * a->sigma));
+    }
+    for (auto &s : a->subs) {
+        o->states += s.states;
+        o->table_bytes += (uint64_t)s.table.size() * 4;
+        o->output_entries += s.out_ids.size();
+        o->smem_states += std::min<uint64_t>(s.states, rows_fit);
+    }
+    o->build_ms = a->build_ms;
+    o->upload_ms = a->upload_ms;
+    o->device = a->device;
+    o->row_len = a->cfg.row_len;
+    o->threads = a->cfg.threads;
+    o->chains = a->cfg.chains;
+    return AC_OK;
+}
+
+int ac_subset(const ac_automaton *a, uint32_t k, ac_subset_view *v) {
+    if (!a || !v || k >= a->K) return set_error(AC_EINVAL, "ac_subset: bad argument");
+    const HostSubset &s = a->subs[k];
+    v->id_lo = s.id_lo;
+    v->id_hi = s.id_hi;
+    v->max_len = s.max_len;
+    v->sigma = a->sigma;
+    v->states = s.states;
+    v->smem_states = 0;
+    v->table = s.table.data();
+    v->fail = s.fail.data();
+    v->depth = s.depth.data();
+    v->out_off = s.out_off.data();
+    v->out_ids = s.out_ids.data();
+    v->symbol_of_byte = a->sym_of_byte;
+    return AC_OK;
+}
+
+int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
+    if (!a || !cfg) return set_error(AC_EINVAL, "ac_set_scan_config: NULL argument");
+    if (cfg->threads && (cfg->threads % 32 || cfg->threads > 512))
+        return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 512");
+    if (cfg->chains && cfg->chains != 1 && cfg->chains != 2 && cfg->chains != 4)
+        return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
+    a->cfg = *cfg;
+    return AC_OK;
+}
+
+int ac_get_scan_config(const ac_automaton *a, ac_scan_config *cfg) {
+    if (!a || !cfg) return set_error(AC_EINVAL, "ac_get_scan_config: NULL argument");
+    *cfg = a->cfg;
+    return AC_OK;
+}
+
+void ac_result_free(ac_result *r) {
+    if (!r) return;
+    free(r->matches);
+    free(r->counts);
+    memset(r, 0, sizeof(*r));
+}
+
+int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int mem, void *stream,
+            ac_result *out) {
+    if (!out) return set_error(AC_EINVAL, "ac_scan: out is NULL");
+    memset(out, 0, sizeof(*out));
+    int rc = check_scan_args(a, n, fmt);
+    if (rc) return rc;
+    if (mem != AC_HOST && mem != AC_DEVICE) return set_error(AC_EINVAL, "ac_scan: unknown memory kind %d", mem);
+    if (!text && n) return set_error(AC_EINVAL, "ac_scan: text is NULL");
+    ac_result r{};
+    r.num_patterns = a->P;
+    r.counts = (uint64_t *)calloc(a->P, sizeof(uint64_t));
+    if (!r.counts) return set_error(AC_ENOMEM, "ac_scan: host counts");
+    if (n == 0) {
+        *out = r;
+        return AC_OK;
+    }
+    DeviceGuard g(a->device);
+    if (!g.ok) {
+        ac_result_free(&r);
+        return set_error(AC_ECUDA, "ac_scan: cannot use device %d", a->device);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = [&]() -> int {
+        Scratch sc(s);
+        const uint64_t nbytes = text_bytes(n, fmt);
+        const uint8_t *d_text = nullptr;
+        int e = stage_text(text, nbytes, mem, s, sc, &d_text);
+        if (e) return e;
+        // counter, error word, counts
+        unsigned long long *num = (unsigned long long *)sc.get(16 + (size_t)a->P * 8);
+        if (!num) return set_error(AC_ENOMEM, "ac_scan: scratch");
+        uint32_t *err = (uint32_t *)(num + 1);
+        unsigned long long *d_counts = num + 2;
+        uint64_t cap = std::min<uint64_t>(n / 256 + 4096, 1ull << 26);
+        ac_scan_config cfg;
+        default_config(a, n, fmt, &cfg);
+        unsigned long long h_num[2];
+        unsigned long long *keys = nullptr;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            keys = (unsigned long long *)sc.get(cap * 8);
+            if (!keys) return set_error(AC_ENOMEM, "ac_scan: %llu output slots", (unsigned long long)cap);
+            CK(cudaMemsetAsync(num, 0, 16 + (size_t)a->P * 8, s), "ac_scan: memset");
+            ScanText t{d_text, n, fmt};
+            ScanOut o{keys, cap, num, d_counts, err};
+            e = launch_scan(a, t, o, cfg, s);
+            if (e) return e;
+            CK(cudaMemcpyAsync(h_num, num, 16, cudaMemcpyDeviceToHost, s), "ac_scan: copy count");
+            CK(cudaStreamSynchronize(s), "ac_scan: scan");
+            if ((uint32_t)h_num[1]) return set_error(AC_ETIMEDOUT, "ac_scan: a device-side wait ran out");
+            if (h_num[0] <= cap) break;
+            sc.release(keys);
+            keys = nullptr;
+            cap = h_num[0];
+        }
+        if (!keys) return set_error(AC_ERANGE, "ac_scan: output beyond capacity after a retry");
+        const uint64_t M = h_num[0];
+        if (M) {
+            unsigned long long *alt = (unsigned long long *)sc.get(M * 8);
+            if (!alt) return set_error(AC_ENOMEM, "ac_scan: sort buffer");
+            const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
+            size_t tb = 0;
+            e = sort_keys(keys, alt, M, end_bit, nullptr, &tb, s, nullptr);
+            if (e) return e;
+            void *temp = sc.get(tb);
+            if (!temp) return set_error(AC_ENOMEM, "ac_scan: sort scratch");
+            unsigned long long *sorted = nullptr;
+            e = sort_keys(keys, alt, M, end_bit, temp, &tb, s, &sorted);
+            if (e) return e;
+            ac_match *d_m = (ac_match *)(sorted == keys ? (void *)alt : (void *)keys);
+            e = launch_keys_to_matches(sorted, num, M, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
+            if (e) return e;
+            r.matches = (ac_match *)malloc(M * sizeof(ac_match));
+            if (!r.matches) return set_error(AC_ENOMEM, "ac_scan: host matches");
+            CK(cudaMemcpyAsync(r.matches, d_m, M * sizeof(ac_match), cudaMemcpyDeviceToHost, s),
+               "ac_scan: copy matches");
+        }
+        CK(cudaMemcpyAsync(r.counts, d_counts, (size_t)a->P * 8, cudaMemcpyDeviceToHost, s), "ac_scan: copy counts");
+        CK(cudaStreamSynchronize(s), "ac_scan: results");
+        r.num_matches = M;
+        return AC_OK;
+    }();
+    if (rc != AC_OK) {
+        ac_result_free(&r);
+        return rc;
+    }
+    *out = r;
+    return AC_OK;
+}
+
+int ac_key_shift(const ac_automaton *a) { return a ? key_shift_for(a) : 0; }
+
+int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                       uint64_t *d_keys, uint64_t cap, uint64_t *d_num, uint64_t *d_counts) {
+    int rc = check_scan_args(a, n, fmt);
+    if (rc) return rc;
+    if ((!d_text && n) || !d_num || (!d_keys && cap)) return set_error(AC_EINVAL, "ac_scan_keys_async: NULL argument");
+    DeviceGuard g(a->device);
+    if (!g.ok) return set_error(AC_ECUDA, "ac_scan_keys_async: cannot use device %d", a->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    const uint8_t *t = nullptr;
+    if (n) {
+        rc = stage_text(d_text, text_bytes(n, fmt), AC_DEVICE, s, sc, &t);
+        if (rc) return rc;
+    }
+    uint32_t *err = (uint32_t *)sc.get(16);
+    if (!err) return set_error(AC_ENOMEM, "ac_scan_keys_async: scratch");
+    CK(cudaMemsetAsync(err, 0, 16, s), "ac_scan_keys_async: memset");
+    CK(cudaMemsetAsync(d_num, 0, 8, s), "ac_scan_keys_async: memset");
+    if (d_counts) CK(cudaMemsetAsync(d_counts, 0, (size_t)a->P * 8, s), "ac_scan_keys_async: memset counts");
+    if (n) {
+        ac_scan_config cfg;
+        default_config(a, n, fmt, &cfg);
+        ScanText tx{t, n, fmt};
+        ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
+                  err};
+        rc = launch_scan(a, tx, o, cfg, s);
+        if (rc) return rc;
+    }
+    return launch_mark_error((unsigned long long *)d_num, err, s);
+}
+
+int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
+                       void *stream, ac_match *d_matches, uint64_t *d_num_out) {
+    if (!a || !d_num || (cap && (!d_keys || !d_matches)))
+        return set_error(AC_EINVAL, "ac_sort_keys_async: NULL argument");
+    if (a->device < 0) return set_error(AC_EINVAL, "ac_sort_keys_async: host-only automaton");
+    DeviceGuard g(a->device);
+    if (!g.ok) return set_error(AC_ECUDA, "ac_sort_keys_async: cannot use device %d", a->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    const uint64_t kcap = cap ? cap : 1;
+    unsigned long long *alt = (unsigned long long *)sc.get(kcap * 8);
+    if (!alt) return set_error(AC_ENOMEM, "ac_sort_keys_async: scratch");
+    int rc = AC_OK;
+    unsigned long long *sorted = (unsigned long long *)d_keys;
+    if (cap) {
+        // entries [M, cap) become the largest key so they sort last
+        rc = launch_pad_keys((unsigned long long *)d_keys, (const unsigned long long *)d_num, cap, s);
+        if (rc) return rc;
+        const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n ? n - 1 : 0));
+        size_t tb = 0;
+        rc = sort_keys((unsigned long long *)d_keys, alt, cap, end_bit, nullptr, &tb, s, nullptr);
+        if (rc) return rc;
+        void *temp = sc.get(tb);
+        if (!temp) return set_error(AC_ENOMEM, "ac_sort_keys_async: sort scratch");
+        rc = sort_keys((unsigned long long *)d_keys, alt, cap, end_bit, temp, &tb, s, &sorted);
+        if (rc) return rc;
+    }
+    return launch_keys_to_matches(sorted, (const unsigned long long *)d_num, cap, (uint32_t)key_shift_for(a),
+                                  d_matches, (unsigned long long *)d_num_out, nullptr, s);
+}
+
+int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                  ac_match *d_matches, uint64_t cap, uint64_t *d_num_matches, uint64_t *d_counts) {
+    int rc = check_scan_args(a, n, fmt);
+    if (rc) return rc;
+    if ((!d_text && n) || !d_num_matches || (!d_matches && cap))
+        return set_error(AC_EINVAL, "ac_scan_async: NULL argument");
+    DeviceGuard g(a->device);
+    if (!g.ok) return set_error(AC_ECUDA, "ac_scan_async: cannot use device %d", a->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    uint64_t *keys = (uint64_t *)sc.get((cap ? cap : 1) * 8);
+    if (!keys) return set_error(AC_ENOMEM, "ac_scan_async: scratch");
+    rc = ac_scan_keys_async(a, d_text, n, fmt, stream, keys, cap, d_num_matches, d_counts);
+    if (rc) return rc;
+    return ac_sort_keys_async(a, n, keys, d_num_matches, cap, stream, d_matches, d_num_matches);
+}
+
+}  // extern "C"

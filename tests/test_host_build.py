@@ -1,0 +1,149 @@
+"""Host-side tests of the library (no GPU): exports, machine construction and
+argument checks.
+
+The machines are built with ``device=-1`` (host only) and walked here in
+numpy, one symbol at a time, and the walk is compared with the oracle; this
+checks the trie, the breadth-first failure function, the output merge, the
+fold into a dense table and the renumbering without any CUDA code running.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from paper_1403_1305_gb300 import ac as A
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ac.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^AC_API\s+[\w\s\*]*?\b(ac_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_function():
+    lib = A.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(A.EXPORTED)
+
+
+def test_version_and_strerror():
+    assert A.ac_version() >= 10000
+    assert A.ac_strerror(A.AC_ERANGE) == "size out of range"
+    assert A.ac_strerror(12345) == "unknown error"
+
+
+def walk(a, text):
+    """Scan `text` with the library's host tables (all subsets), in numpy."""
+    st = A.ac_stats(a)
+    res = []
+    for k in range(st["num_subsets"]):
+        v = A.ac_subset(a, k)
+        T, off, ids, sym = v["table"], v["out_off"], v["out_ids"], v["symbol_of_byte"]
+        sigma = v["sigma"]
+        s = 0
+        tb = np.frombuffer(text, np.uint8) if isinstance(text, bytes) else np.asarray(text, dtype=np.uint8)
+        for i, b in enumerate(tb.tolist()):
+            c = sym[b]
+            e = int(T[s, c]) if c < sigma else 0
+            s = e & 0x7FFFFFFF
+            if e >> 31:
+                res += [(i, int(j)) for j in ids[off[s]:off[s + 1]]]
+            else:
+                assert off[s + 1] == off[s]
+    res.sort()
+    return np.asarray(res, dtype=np.uint32).reshape(-1, 2)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_host_tables_match_oracle_on_random_cases(K):
+    rng = np.random.default_rng(100 + K)
+    for i in range(300):
+        text, pats = workloads.tiny_case(rng, b"ACGT" if i % 2 else b"ab", max_n=80, max_p=9, max_len=6,
+                                         other_frac=0.1 if i % 4 == 0 else 0.0)
+        if len(pats) < K:
+            continue
+        a = A.ac_build(pats, num_subsets=K, device=-1)
+        want, _ = oracle.scan(pats, text)
+        assert np.array_equal(walk(a, text), want), (i, pats, bytes(text))
+
+
+def test_worked_examples_on_host_tables():
+    for pats, text, want in (([b"AB", b"ABG", b"BEDE", b"EF"], b"ABEDE", [[1, 0], [4, 2]]),
+                             ([b"HE", b"HIS", b"SHE", b"HERS"], b"USHERS", [[3, 0], [3, 2], [5, 3]])):
+        a = A.ac_build(pats, device=-1)
+        assert walk(a, text).tolist() == want
+
+
+def test_breadth_first_numbering_and_failure_function():
+    w = workloads.config1(n=1 << 14, P=60)
+    a = A.ac_build(w.patterns, alphabet="ACGT", device=-1)
+    v = A.ac_subset(a, 0)
+    m = oracle.Machine(w.patterns)
+    assert v["states"] == m.num_states           # same goto function, renumbered
+    depth, fail = v["depth"], v["fail"]
+    assert depth[0] == 0 and fail[0] == 0
+    assert np.all(np.diff(depth.astype(np.int64)) >= 0)     # breadth-first order
+    assert np.all(depth[fail[1:]] < depth[1:])             # failure goes shallower
+    # every state's output holds exactly the patterns that are suffixes of its string
+    strings = {0: b""}
+    T = v["table"]
+    for s in range(v["states"]):
+        for c in range(4):
+            t = int(T[s, c]) & 0x7FFFFFFF
+            if depth[t] == depth[s] + 1 and t not in strings:
+                strings[t] = strings[s] + b"ACGT"[c:c + 1]
+    assert len(strings) == v["states"]
+    off, ids = v["out_off"], v["out_ids"]
+    for s, string in list(strings.items())[:400]:
+        want = sorted(j for j, p in enumerate(w.patterns) if string.endswith(p))
+        assert ids[off[s]:off[s + 1]].tolist() == want
+
+
+def test_subset_split_is_contiguous_and_balanced():
+    pats = [bytes([65 + i % 4]) * (1 + i // 4) for i in range(10)]
+    a = A.ac_build(pats, num_subsets=4, device=-1)
+    ranges = [(A.ac_subset(a, k)["id_lo"], A.ac_subset(a, k)["id_hi"]) for k in range(4)]
+    assert ranges[0][0] == 0 and ranges[-1][1] == 10
+    assert all(ranges[i][1] == ranges[i + 1][0] for i in range(3))
+    sizes = [h - l for l, h in ranges]
+    assert max(sizes) - min(sizes) <= 1
+
+
+def test_argument_errors():
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([], device=-1)
+    assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([b"A", b""], device=-1)
+    assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([b"A", b"C"], num_subsets=3, device=-1)
+    assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([b"ACGN"], alphabet="ACGT", device=-1)
+    assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([b"AC"], alphabet="AAC", device=-1)
+    assert e.value.code == A.AC_EINVAL
+    a = A.ac_build([b"AC"], device=-1)
+    with pytest.raises(A.AcError) as e:
+        A.ac_scan(a, b"ACAC")                 # host-only automaton cannot scan
+    assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError):
+        A.ac_set_scan_config(a, threads=48)
+    with pytest.raises(A.AcError):
+        A.ac_set_scan_config(a, chains=3)
+
+
+def test_explicit_alphabet_order_sets_symbol_codes():
+    a = A.ac_build([b"GATTACA"], alphabet="ACGT", device=-1)
+    sym = A.ac_subset(a, 0)["symbol_of_byte"]
+    assert [sym[ord(c)] for c in "ACGT"] == [0, 1, 2, 3]
+    assert sym[ord("N")] == 4
