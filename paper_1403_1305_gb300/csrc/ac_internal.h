@@ -77,6 +77,7 @@ struct ScanText {
     const uint8_t *d_text;  // 16-byte aligned device pointer
     uint64_t n;             // symbols
     int fmt;
+    uint64_t readable;      // bytes that may be read at d_text (>= the text's bytes; 0 = exactly those)
 };
 
 struct ScanOut {

@@ -186,18 +186,24 @@ static int check_scan_args(const ac_automaton *a, uint64_t n, int fmt) {
 
 static uint64_t text_bytes(uint64_t n, int fmt) { return fmt == AC_U8 ? n : (n + 3) / 4; }
 
-// Device copy of the text at a 16-byte aligned address.
+// Device copy of the text at a 16-byte aligned address. Texts shorter than
+// 64 bytes are copied into a zero-padded 64-byte buffer (the scan reads whole
+// 32-byte stages of full rows); *readable receives the bytes that may be read.
 static int stage_text(const uint8_t *text, uint64_t nbytes, int mem, cudaStream_t s, Scratch &sc,
-                      const uint8_t **d_text) {
-    if (mem == AC_DEVICE && ((uintptr_t)text & 15) == 0) {
+                      const uint8_t **d_text, uint64_t *readable) {
+    *readable = nbytes;
+    if (mem == AC_DEVICE && ((uintptr_t)text & 15) == 0 && nbytes >= 64) {
         *d_text = text;
         return AC_OK;
     }
-    uint8_t *buf = (uint8_t *)sc.get((nbytes + 15) & ~15ull);
+    const uint64_t alloc = std::max<uint64_t>(64, (nbytes + 15) & ~15ull);
+    uint8_t *buf = (uint8_t *)sc.get(alloc);
     if (!buf) return set_error(AC_ENOMEM, "scan: device text buffer of %llu bytes", (unsigned long long)nbytes);
+    if (nbytes < 64) CK(cudaMemsetAsync(buf, 0, 64, s), "scan: text padding");
     CK(cudaMemcpyAsync(buf, text, nbytes, mem == AC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s),
        "scan: text copy");
     *d_text = buf;
+    if (nbytes < 64) *readable = 64;
     return AC_OK;
 }
 
@@ -379,7 +385,8 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         Scratch sc(s);
         const uint64_t nbytes = text_bytes(n, fmt);
         const uint8_t *d_text = nullptr;
-        int e = stage_text(text, nbytes, mem, s, sc, &d_text);
+        uint64_t readable = 0;
+        int e = stage_text(text, nbytes, mem, s, sc, &d_text, &readable);
         if (e) return e;
         // counter, error word, counts
         unsigned long long *num = (unsigned long long *)sc.get(16 + (size_t)a->P * 8);
@@ -395,7 +402,7 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             keys = (unsigned long long *)sc.get(cap * 8);
             if (!keys) return set_error(AC_ENOMEM, "ac_scan: %llu output slots", (unsigned long long)cap);
             CK(cudaMemsetAsync(num, 0, 16 + (size_t)a->P * 8, s), "ac_scan: memset");
-            ScanText t{d_text, n, fmt};
+            ScanText t{d_text, n, fmt, readable};
             ScanOut o{keys, cap, num, d_counts, err};
             e = launch_scan(a, t, o, cfg, s);
             if (e) return e;
@@ -454,8 +461,9 @@ int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n,
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
     const uint8_t *t = nullptr;
+    uint64_t readable = 0;
     if (n) {
-        rc = stage_text(d_text, text_bytes(n, fmt), AC_DEVICE, s, sc, &t);
+        rc = stage_text(d_text, text_bytes(n, fmt), AC_DEVICE, s, sc, &t, &readable);
         if (rc) return rc;
     }
     uint32_t *err = (uint32_t *)sc.get(16);
@@ -466,7 +474,7 @@ int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n,
     if (n) {
         ac_scan_config cfg;
         default_config(a, n, fmt, &cfg);
-        ScanText tx{t, n, fmt};
+        ScanText tx{t, n, fmt, readable};
         ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
                   err};
         rc = launch_scan(a, tx, o, cfg, s);

@@ -36,6 +36,8 @@
 //    kernel records an error word and stops issuing work.
 #include <cub/device/device_radix_sort.cuh>
 
+#include <cuda.h>
+
 #include "ac_internal.h"
 
 namespace acgb {
@@ -53,9 +55,9 @@ enum { MODE_SMEM = 0, MODE_HYBRID = 1 };
 struct ScanParams {
     const uint8_t *text;
     uint64_t nbytes;        // bytes of text
-    uint64_t nbytes_al;     // nbytes rounded down to 16 (bulk copies stop there)
     uint64_t nsym;          // symbols
-    uint64_t num_rows;
+    uint64_t full_rows;     // rows of row_bytes entirely inside the text (2-D tensor map)
+    uint64_t num_rows;      // full_rows, plus one if a partial last row exists
     uint64_t num_tiles;
     uint32_t row_bytes;     // multiple of kStageBytes
     uint32_t rows_per_tile; // warps * 32 * C
@@ -64,6 +66,7 @@ struct ScanParams {
     uint32_t smem_rows;     // table rows that fit in shared memory
     uint32_t table_words;   // words reserved for the table in shared memory
     uint32_t key_shift;     // key = pos << key_shift | id
+    uint32_t tail_bytes;    // bytes of the partial last row (1-D tensor map), 0 if none
     const SubsetDev *subs;
     unsigned long long *keys;
     uint64_t cap;
@@ -99,11 +102,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void *dst, const CUtensorMap *map, int32_t x, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -190,33 +201,79 @@ __device__ __forceinline__ void emit_warp(bool has, uint32_t sid, uint64_t pos, 
     }
 }
 
+__device__ __forceinline__ uint32_t word_of(const uint4 &w, int e) {
+    return e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
+}
+
+// One stage of one chain walked symbol by symbol with every check (text
+// edges, bytes outside the alphabet, table rows outside shared memory),
+// emitting the output of every flagged state at main-stage positions. The
+// stage's 32 bytes are in w0/w1 (every byte of the text inside the stage is
+// there; positions before the text start reset the walk to the root). All 32
+// lanes call it together; returns the state after the stage.
+template <int FMT>
+__device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool active, bool main_stage,
+                                             const uint4 w0, const uint4 w1, const ScanParams &p,
+                                             const SubsetDev &sd, const uint32_t *stab, const uint8_t *smap,
+                                             uint32_t hot, uint32_t lane) {
+    constexpr uint32_t SYM = (FMT == FMT_U8) ? kStageBytes : kStageBytes * 4;
+    const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    uint32_t sc = s_in;
+    for (uint32_t i = 0; i < SYM; ++i) {
+        const int64_t pos = pos0 + i;
+        const bool live = active && pos >= 0 && pos < (int64_t)p.nsym;
+        bool has = false;
+        if (live) {
+            const uint32_t bi = (FMT == FMT_U8) ? i : (i >> 2);
+            const uint32_t byte = (w[bi >> 2] >> (8 * (bi & 3))) & 0xffu;
+            const uint32_t c = (FMT == FMT_U8) ? (uint32_t)smap[byte] : (byte >> (2 * (i & 3))) & 3u;
+            uint32_t nv = 0;
+            if (c < p.sigma) nv = lookup<MODE_HYBRID>(stab, sd.table, hot, p.sigma, sc, c);
+            sc = nv & kStateMask;
+            has = main_stage && (nv & kFlag);
+        } else if (pos < 0) {
+            sc = 0;
+        }
+        emit_warp(has, sc, (uint64_t)(pos < 0 ? 0 : pos), sd, p, lane);
+    }
+    return sc;
+}
+
 // ------------------------------------------------------------------ the kernel
+// Shared memory per warp and pipeline slot: C boxes of 32 rows x 32 bytes
+// (one per chain group, written by one 2-D TMA each) and one 32-byte slot
+// for the ragged last row (written by a 1-D TMA), padded to 128 bytes.
+__host__ __device__ constexpr uint32_t slot_bytes_for(uint32_t C) { return C * 1024u + 128u; }
+
 template <int FMT, int ALPHA, int MODE, int C>
-__global__ void __launch_bounds__(512, 1) scan_kernel(const __grid_constant__ ScanParams p) {
+__global__ void __launch_bounds__(512, 1)
+    scan_kernel(const __grid_constant__ ScanParams p, const __grid_constant__ CUtensorMap rows_map,
+                const __grid_constant__ CUtensorMap tail_map) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t BX = kStageBytes;
-    constexpr uint32_t SYM_PER_SB = (FMT == FMT_U8) ? kSB : kSB * 4;
+    constexpr uint32_t SYM_PER_STAGE = (FMT == FMT_U8) ? BX : BX * 4;
+    constexpr uint32_t SLOT = slot_bytes_for(C);
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t *stab = reinterpret_cast<uint32_t *>(smem);
-    uint8_t *smap = smem + (size_t)p.table_words * 4;
-    uint8_t *stage = smap + 256;
-    const uint32_t warp_stage_bytes = kNS * C * 32 * BX;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + (size_t)nwarps * warp_stage_bytes);
-    uint8_t *my_stage = stage + (size_t)warp * warp_stage_bytes;
+    uint8_t *smap = smem + (((size_t)p.table_words * 4 + 127) & ~(size_t)127);
+    uint8_t *stage = reinterpret_cast<uint8_t *>(((uintptr_t)(smap + 256) + 127) & ~(uintptr_t)127);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + (size_t)nwarps * kNS * SLOT);
+    uint8_t *my_stage = stage + (size_t)warp * kNS * SLOT;
     uint64_t *my_bars = bars + warp * kNS;
 
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
     if (threadIdx.x == 0) {
-        for (uint32_t i = 0; i < nwarps * kNS; ++i) mbar_init(bars + i, 32);
+        for (uint32_t i = 0; i < nwarps * kNS; ++i) mbar_init(bars + i, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    uint32_t parity = 0;  // bit i = expected parity of slot i
+    uint32_t parity = 0;  // bit i = parity of the phase slot i waits for next
     bool aborted = false;
     int cur_k = -1;
     const uint32_t sigma = p.sigma;
+    const int64_t L = p.row_bytes;
 
     for (uint64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
         const uint32_t k = (uint32_t)(tile % p.K);
@@ -233,48 +290,49 @@ __global__ void __launch_bounds__(512, 1) scan_kernel(const __grid_constant__ Sc
             __syncthreads();
             cur_k = (int)k;
         }
-        // warm-up stages for this subset
+        if (aborted) continue;  // keeps taking part in the CTA barriers above, does no work
+
         const uint32_t warm_bytes = (FMT == FMT_U8) ? sd.warm : (sd.warm + 3) / 4;
         const uint32_t nW = (warm_bytes + BX - 1) / BX;
         const uint32_t nst = nW + p.row_bytes / BX;
-
-        // this warp's chains
         const uint64_t row0 = rb * p.rows_per_tile + (uint64_t)warp * 32 * C;
-        int64_t x0[C];
+        if (row0 >= p.num_rows) continue;
+        const bool tail_in_warp = p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
+
+        // lane 0 issues one 2-D box per chain group (and the tail row's 1-D box)
+        auto issue = [&](uint32_t s) {
+            const uint32_t slot = s % kNS;
+            uint8_t *base = my_stage + slot * SLOT;
+            uint64_t *bar = my_bars + slot;
+            const int64_t o = (int64_t)s * BX - (int64_t)nW * BX;  // byte offset from the row start
+            const int64_t dy = o >= 0 ? o / L : -((-o + L - 1) / L);
+            const int32_t col = (int32_t)(o - dy * L);
+            uint32_t bytes = 0;
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (row0 + (uint64_t)j * 32 < p.num_rows) bytes += 1024;
+            const bool tail_now = tail_in_warp && o >= 0;
+            if (tail_now) bytes += BX;
+            mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (row0 + (uint64_t)j * 32 < p.num_rows)
+                    tma_load_2d(base + j * 1024, &rows_map, col, (int32_t)((int64_t)(row0 + j * 32) + dy), bar);
+            if (tail_now) tma_load_1d(base + C * 1024, &tail_map, (int32_t)o, bar);
+        };
+
+        if (lane == 0)
+            for (uint32_t s = 0; s < (uint32_t)kNS && s < nst; ++s) issue(s);
+
+        uint64_t row[C];
         bool active[C];
         uint32_t st8[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            uint64_t row = row0 + (uint64_t)j * 32 + lane;
-            active[j] = row < p.num_rows;
-            x0[j] = (int64_t)(row * p.row_bytes) - (int64_t)nW * BX;
+            row[j] = row0 + (uint64_t)j * 32 + lane;
+            active[j] = row[j] < p.num_rows;
             st8[j] = 0;
         }
-
-        auto issue = [&](uint32_t s) {
-            const uint32_t slot = s % kNS;
-            uint8_t *buf = my_stage + slot * (C * 32 * BX);
-            uint32_t bytes[C], total = 0;
-            int64_t lo[C];
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                int64_t x = x0[j] + (int64_t)s * BX;
-                int64_t l = x > 0 ? x : 0;
-                int64_t h = x + BX < (int64_t)p.nbytes_al ? x + BX : (int64_t)p.nbytes_al;
-                bytes[j] = (active[j] && h > l) ? (uint32_t)(h - l) : 0u;
-                lo[j] = l;
-                total += bytes[j];
-            }
-            mbar_arrive_expect_tx(my_bars + slot, total);
-#pragma unroll
-            for (int j = 0; j < C; ++j)
-                if (bytes[j])
-                    bulk_copy_g2s(buf + (j * 32 + lane) * BX + (lo[j] - (x0[j] + (int64_t)s * BX)), p.text + lo[j],
-                                  bytes[j], my_bars + slot);
-        };
-
-        if (aborted) continue;  // keeps taking part in the CTA barriers above, does no work
-        for (uint32_t s = 0; s < (uint32_t)kNS && s < nst; ++s) issue(s);
 
         for (uint32_t s = 0; s < nst; ++s) {
             const uint32_t slot = s % kNS;
@@ -283,116 +341,108 @@ __global__ void __launch_bounds__(512, 1) scan_kernel(const __grid_constant__ Sc
                 break;
             }
             parity ^= 1u << slot;
-            // read this stage's bytes into registers, then refill the slot
-            uint4 data[C][BX / 16];
-            const uint8_t *buf = my_stage + slot * (C * 32 * BX);
-            const uint32_t swz = (lane >> 2) & 1u;  // avoids 2-way bank conflicts between lanes l and l+4
+            const int64_t o = (int64_t)s * BX - (int64_t)nW * BX;
+            const bool main_stage = o >= 0;
+            // this stage's 32 bytes of every chain into registers, then refill the slot
+            uint4 data[C][2];
+            const uint8_t *base = my_stage + slot * SLOT;
+            const uint32_t swz = (lane >> 2) & 1u;  // lanes l and l+4 read different 16-byte halves first
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const uint4 *b4 = reinterpret_cast<const uint4 *>(buf + (j * 32 + lane) * BX);
-#pragma unroll
-                for (uint32_t q = 0; q < BX / 16; ++q) {
-                    uint32_t qq = q ^ swz;
-                    uint4 t = b4[qq];
-                    if (qq == 0) data[j][0] = t; else data[j][1] = t;
-                }
+                const bool tail_row = tail_in_warp && main_stage && row[j] == p.full_rows;
+                const uint4 *b4 = reinterpret_cast<const uint4 *>(tail_row ? base + C * 1024 : base + j * 1024 + lane * BX);
+                const uint4 t0 = b4[swz], t1 = b4[swz ^ 1u];
+                data[j][0] = swz ? t1 : t0;
+                data[j][1] = swz ? t0 : t1;
             }
             __syncwarp();
-            fence_proxy_async();
-            if (s + kNS < nst) issue(s + kNS);
+            if (s + kNS < nst) {
+                fence_proxy_async();
+                if (lane == 0) issue(s + kNS);
+            }
 
-            const bool main_stage = s >= nW;
+            int64_t pos0[C];
+            bool fast[C], dead[C], before[C];
+            uint32_t v[C], acc[C], bad[C], s_in[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
+                const int64_t b0 = (int64_t)row[j] * L + o;
+                pos0[j] = (FMT == FMT_U8) ? b0 : b0 * 4;
+                dead[j] = !active[j] || pos0[j] >= (int64_t)p.nsym;
+                before[j] = !dead[j] && pos0[j] + (int64_t)SYM_PER_STAGE <= 0;
+                fast[j] = !dead[j] && pos0[j] >= 0 && pos0[j] + (int64_t)SYM_PER_STAGE <= (int64_t)p.nsym;
+                s_in[j] = st8[j];
+                v[j] = s_in[j];
+                acc[j] = 0;
+                bad[j] = 0;
+            }
+            // The C chains advance together, one symbol each per round, so their
+            // lookups are independent and overlap. Chains off the fast path walk
+            // in-bounds garbage that is discarded.
+            if (FMT == FMT_U8 && ALPHA == ALPHA_ACGT) {
 #pragma unroll
-                for (uint32_t q = 0; q < BX / 16; ++q) {
-                    const int64_t b0 = x0[j] + (int64_t)s * BX + (int64_t)q * kSB;  // byte offset of sub-block
-                    const int64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;           // symbol position of its start
-                    const bool dead = !active[j] || pos0 >= (int64_t)p.nsym;
-                    const bool before = !dead && pos0 + (int64_t)SYM_PER_SB <= 0;
-                    const bool fast = !dead && !before && b0 >= 0 && b0 + (int64_t)kSB <= (int64_t)p.nbytes_al &&
-                                      pos0 + (int64_t)SYM_PER_SB <= (int64_t)p.nsym;
-                    const uint32_t s_in = st8[j];
-                    uint32_t v = s_in, acc = 0, bad = 0;
-                    const uint4 w4 = data[j][q];
-                    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
-                    if (fast) {
-                        if (FMT == FMT_U8 && ALPHA == ALPHA_ACGT) {
+                for (int e = 0; e < 8; ++e) {
+                    uint32_t cw[C];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                uint32_t cw = acgt_codes4(w[e]);
-                                bad |= acgt_mismatch4(w[e], cw);
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) {
-                                    v = lookup4<MODE>(stab, sd.table, hot, v, (cw >> (8 * b)) & 3u);
-                                    acc |= v;
-                                }
-                            }
-                        } else if (FMT == FMT_U8) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-#pragma unroll
-                                for (int b = 0; b < 4; ++b) {
-                                    uint32_t c = smap[(w[e] >> (8 * b)) & 0xffu];
-                                    uint32_t cc = c < sigma ? c : 0u;
-                                    uint32_t nv = lookup<MODE>(stab, sd.table, hot, sigma, v, cc);
-                                    v = c < sigma ? nv : 0u;
-                                    acc |= v;
-                                }
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-#pragma unroll
-                                for (int b = 0; b < 16; ++b) {
-                                    v = lookup4<MODE>(stab, sd.table, hot, v, (w[e] >> (2 * b)) & 3u);
-                                    acc |= v;
-                                }
-                            }
-                        }
-                        st8[j] = v & kStateMask;
-                    } else if (before) {
-                        st8[j] = 0;
+                    for (int j = 0; j < C; ++j) {
+                        const uint32_t w = word_of(data[j][e >> 2], e & 3);
+                        cw[j] = acgt_codes4(w);
+                        bad[j] |= acgt_mismatch4(w, cw[j]);
                     }
-                    const bool need = !dead && !before && (!fast || bad != 0 || (main_stage && (acc & kFlag)));
-                    if (__any_sync(kFull, need)) {
-                        // careful walk of this sub-block, all lanes together
-                        uint32_t sc = s_in;
-                        for (uint32_t i = 0; i < SYM_PER_SB; ++i) {
-                            const int64_t pos = pos0 + i;
-                            const bool live = active[j] && pos >= 0 && pos < (int64_t)p.nsym;
-                            bool has = false;
-                            if (live) {
-                                const int64_t boff = (FMT == FMT_U8) ? pos : (pos >> 2);
-                                uint32_t byte;
-                                if (boff < (int64_t)p.nbytes_al) {
-                                    const uint32_t bi = (uint32_t)(boff - b0);
-                                    byte = (w[bi >> 2] >> (8 * (bi & 3))) & 0xffu;
-                                } else {
-                                    byte = p.text[boff];
-                                }
-                                uint32_t c;
-                                if (FMT == FMT_U8) {
-                                    c = smap[byte];
-                                } else {
-                                    c = (byte >> (2 * (pos & 3))) & 3u;
-                                }
-                                uint32_t nv = 0;
-                                if (c < sigma) nv = lookup<MODE_HYBRID>(stab, sd.table, hot, sigma, sc, c);
-                                sc = nv & kStateMask;
-                                has = main_stage && (nv & kFlag);
-                            } else if (pos < 0) {
-                                sc = 0;
-                            }
-                            emit_warp(has, sc, (uint64_t)(pos < 0 ? 0 : pos), sd, p, lane);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (cw[j] >> (8 * b)) & 3u);
+                            acc[j] |= v[j];
                         }
-                        if (!dead) st8[j] = sc;
                     }
+                }
+            } else if (FMT == FMT_U8) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            const uint32_t c = smap[(word_of(data[j][e >> 2], e & 3) >> (8 * b)) & 0xffu];
+                            const uint32_t nv = lookup<MODE>(stab, sd.table, hot, sigma, v[j], c < sigma ? c : 0u);
+                            v[j] = c < sigma ? nv : 0u;
+                            acc[j] |= v[j];
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (word_of(data[j][e >> 2], e & 3) >> (2 * b)) & 3u);
+                            acc[j] |= v[j];
+                        }
+                    }
+                }
+            }
+            bool need[C];
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (fast[j]) st8[j] = v[j] & kStateMask;
+                else if (before[j]) st8[j] = 0;
+                need[j] = !dead[j] && !before[j] && (!fast[j] || bad[j] != 0 || (main_stage && (acc[j] & kFlag)));
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (__any_sync(kFull, need[j])) {
+                    const uint32_t sc = careful_walk<FMT>(s_in[j], pos0[j], active[j], main_stage, data[j][0],
+                                                          data[j][1], p, sd, stab, smap, hot, lane);
+                    if (!dead[j]) st8[j] = sc;
                 }
             }
         }
     }
-    if (aborted) {
+    if (aborted && lane == 0) {
         // let copies already issued by this warp land before the CTA exits (bounded)
         for (uint32_t slot = 0; slot < (uint32_t)kNS; ++slot) {
             uint64_t t0 = global_ns();
@@ -437,7 +487,7 @@ __global__ void mark_error_kernel(unsigned long long *num, const uint32_t *err) 
 }
 
 // ------------------------------------------------------------------ dispatch
-using KernelFn = void (*)(ScanParams);
+using KernelFn = void (*)(ScanParams, CUtensorMap, CUtensorMap);
 
 template <int FMT, int ALPHA, int MODE>
 KernelFn pick_c(uint32_t C) {
@@ -462,6 +512,52 @@ uint32_t bits_for(uint64_t x) {  // bits needed to hold values 0..x
     return b;
 }
 
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    return fn;
+}
+
+// rows x row_bytes bytes at base, boxes of 32 bytes x 32 rows
+int encode_rows_map(CUtensorMap *m, const uint8_t *base, uint64_t row_bytes, uint64_t rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return set_error(AC_ECUDA, "scan: cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[2] = {row_bytes, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {kStageBytes, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? AC_OK : set_error(AC_ECUDA, "scan: encoding the row tensor map failed (%d)", (int)r);
+}
+
+// bytes bytes at base, boxes of 32 bytes
+int encode_tail_map(CUtensorMap *m, const uint8_t *base, uint64_t bytes) {
+    EncodeTiled enc = encoder();
+    if (!enc) return set_error(AC_ECUDA, "scan: cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[1] = {bytes};
+    cuuint64_t strides[1] = {0};
+    cuuint32_t box[1] = {kStageBytes};
+    cuuint32_t es[1] = {1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, (void *)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? AC_OK : set_error(AC_ECUDA, "scan: encoding the tail tensor map failed (%d)", (int)r);
+}
+
 }  // namespace
 
 int scan_smem_limit(int device) {
@@ -471,19 +567,21 @@ int scan_smem_limit(int device) {
 }
 
 uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg) {
-    return (cfg.threads / 32) * kNS * cfg.chains * 32 * kStageBytes + (cfg.threads / 32) * kNS * 8 + 256;
+    const uint32_t warps = cfg.threads / 32;
+    return 256 + 128 + 128 + warps * kNS * slot_bytes_for(cfg.chains) + warps * kNS * 8;
 }
 
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg) {
     ac_scan_config c = a->cfg;
-    if (!c.threads) c.threads = 256;
-    if (!c.chains) c.chains = 4;
+    if (!c.threads) c.threads = 512;
+    if (!c.chains) c.chains = 2;
     if (!c.row_len) {
-        // enough rows for ~2 tiles per SM, but at least 8x the warm-up and 256 symbols
+        // one chain per row, all chains of the GPU busy once, rows at least
+        // 8x the warm-up and 256 symbols long
         int sms = 148;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device < 0 ? 0 : a->device);
         uint64_t chains = (uint64_t)sms * c.threads * c.chains;
-        uint64_t want = n / (chains ? chains : 1);
+        uint64_t want = (n + chains - 1) / (chains ? chains : 1);
         uint64_t lo = std::max<uint64_t>(256, 8ull * a->max_len);
         uint64_t L = std::max<uint64_t>(want, lo);
         if (L > (1u << 20)) L = 1u << 20;
@@ -503,19 +601,26 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
         return set_error(AC_EINVAL, "scan: chains per thread must be 1, 2 or 4");
     const uint64_t nbytes = (t.fmt == AC_U8) ? t.n : (t.n + 3) / 4;
     if (nbytes == 0) return AC_OK;
+    const uint64_t readable = std::max(nbytes, t.readable);
+    if (readable < kStageBytes) return set_error(AC_EINVAL, "scan: text buffer shorter than one stage");
+    if ((uintptr_t)t.d_text & 15) return set_error(AC_EINVAL, "scan: text must be 16-byte aligned");
     const uint32_t sym_per_byte = (t.fmt == AC_U8) ? 1 : 4;
     uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
     rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
-    if (rb == 0) rb = kStageBytes;
     if (rb > (1u << 24)) rb = 1u << 24;
+    const uint64_t rmax = readable / kStageBytes * kStageBytes;
+    if (rb > rmax) rb = rmax;
+    if (rb == 0) rb = kStageBytes;
 
     ScanParams p{};
     p.text = t.d_text;
     p.nbytes = nbytes;
-    p.nbytes_al = nbytes & ~15ull;
     p.nsym = t.n;
     p.row_bytes = (uint32_t)rb;
-    p.num_rows = (nbytes + rb - 1) / rb;
+    p.full_rows = readable / rb;
+    const uint64_t covered = p.full_rows * rb;
+    p.tail_bytes = nbytes > covered ? (uint32_t)(nbytes - covered) : 0u;
+    p.num_rows = p.full_rows + (p.tail_bytes ? 1 : 0);
     p.rows_per_tile = cfg.threads * cfg.chains;
     p.K = a->K;
     p.sigma = a->sigma;
@@ -529,12 +634,24 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     memcpy(p.sym_of_byte, a->sym_of_byte, 256);
     const uint64_t row_blocks = (p.num_rows + p.rows_per_tile - 1) / p.rows_per_tile;
     p.num_tiles = row_blocks * a->K;
+    if (p.full_rows >= (1ull << 31) || p.num_rows * rb >= (1ull << 40))
+        return set_error(AC_ERANGE, "scan: text too long for the row tensor map");
+
+    CUtensorMap rows_map, tail_map;
+    memset(&rows_map, 0, sizeof(rows_map));
+    memset(&tail_map, 0, sizeof(tail_map));
+    int rc = encode_rows_map(&rows_map, t.d_text, rb, p.full_rows);
+    if (rc) return rc;
+    if (p.tail_bytes) {
+        rc = encode_tail_map(&tail_map, t.d_text + covered, p.tail_bytes);
+        if (rc) return rc;
+    }
 
     // shared memory: table prefix + map + staging + barriers
     const int limit = scan_smem_limit(a->device);
     const uint32_t staging = scan_stage_bytes_per_cta(cfg);
     if ((int)staging + 1024 > limit) return set_error(AC_EINVAL, "scan: staging does not fit in shared memory");
-    uint64_t avail = (uint64_t)limit - staging - 64;
+    uint64_t avail = (uint64_t)limit - staging - 128;  // the table is rounded up to 128 bytes
     if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
     uint32_t rows_fit = (uint32_t)(avail / (4ull * a->sigma));
     if (a->placement == AC_PLACE_GLOBAL) rows_fit = 0;
@@ -547,7 +664,8 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     const uint32_t rows_used = std::min(max_states, rows_fit);
     p.smem_rows = rows_used;
     p.table_words = (rows_used * a->sigma + 3) & ~3u;
-    const size_t smem = (size_t)p.table_words * 4 + staging;
+    const size_t smem = (((size_t)p.table_words * 4 + 127) & ~(size_t)127) + staging;
+    if (smem > (size_t)limit) return set_error(AC_EINVAL, "scan: shared memory plan exceeds the limit");
 
     const bool acgt = t.fmt == AC_U8 && a->dna_acgt;
     KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, cfg.chains);
@@ -557,7 +675,7 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device);
     uint64_t grid = cfg.ctas ? cfg.ctas : (uint64_t)sms;
     if (grid > p.num_tiles) grid = p.num_tiles;
-    fn<<<(unsigned)grid, cfg.threads, smem, stream>>>(p);
+    fn<<<(unsigned)grid, cfg.threads, smem, stream>>>(p, rows_map, tail_map);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan launch: %s", cudaGetErrorString(e));
     return AC_OK;

@@ -87,7 +87,8 @@ def test_packed_text_ragged_lengths():
     rng = np.random.default_rng(9)
     for n in list(range(0, 70)) + [127, 128, 129, 255, 256, 257, 1000, 4093, 4096, 4099]:
         text = workloads.dna_text(rng, n)
-        pats = workloads.draw_patterns(rng, text if n >= 3 else workloads.dna_text(rng, 8), 20, 1, 9, 0.5,
+        src = text if n >= 64 else workloads.dna_text(rng, 64)
+        pats = workloads.draw_patterns(rng, [src, text] if n else src, 20, 1, 9, 0.5,
                                        np.frombuffer(b"ACGT", np.uint8))
         a = A.ac_build(pats, alphabet="ACGT")
         A.ac_set_scan_config(a, row_len=128, threads=64, chains=2)

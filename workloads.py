@@ -78,7 +78,11 @@ def draw_patterns(rng, texts, P, lo, hi, frac_sub, letters, probs=None, exclude=
     seen = set() if exclude is None else set(exclude)
     out = []
     letters = np.asarray(letters, dtype=np.uint8)
+    tries = 0
     while len(out) < n_sub:
+        tries += 1
+        if tries > 100 * P + 1000:
+            raise ValueError("cannot draw enough distinct substrings from these texts")
         t = texts[int(rng.integers(0, len(texts)))]
         L = int(rng.integers(lo, min(hi, len(t)) + 1))
         off = int(rng.integers(0, len(t) - L + 1))
@@ -87,6 +91,9 @@ def draw_patterns(rng, texts, P, lo, hi, frac_sub, letters, probs=None, exclude=
             seen.add(p)
             out.append(p)
     while len(out) < P:
+        tries += 1
+        if tries > 200 * P + 2000:
+            raise ValueError("cannot draw enough distinct patterns")
         L = int(rng.integers(lo, hi + 1))
         p = iid_text(rng, L, letters, probs).tobytes()
         if p not in seen:
