@@ -213,6 +213,26 @@ AC_API int ac_key_shift(const ac_automaton *a);
 AC_API int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num,
                               uint64_t cap, void *stream, ac_match *d_matches, uint64_t *d_num_out);
 
+/* ac_scan_noalloc: the same scan as ac_scan_async, for callers that must
+ * not allocate device memory while scanning (the paper has no counterpart;
+ * this is a deployment convenience). Some callers cannot call cudaMalloc or
+ * cudaMallocAsync at that point: a process whose device memory was reserved
+ * in advance by another allocator, a latency-critical loop that cannot take
+ * an allocation's implicit synchronisation or lock, or a host application
+ * that forbids the library any allocation. This entry point allocates
+ * nothing; its scratch is one fixed array of about 8.1 MiB compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits. Limits: cap <= 262,144 match records (larger cap: AC_ERANGE); the
+ * text must be 16-byte aligned unless it is at most 65,536 bytes (else
+ * AC_EINVAL). The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents
+ * (the call clears what must start at zero): calls that overlap on the GPU,
+ * from any stream or thread, race and must be serialised by the caller.
+ * Arguments, outputs and errors are otherwise those of ac_scan_async. */
+AC_API int ac_scan_noalloc(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                           ac_match *d_matches, uint64_t cap, uint64_t *d_num_matches, uint64_t *d_counts);
+
 /* One text of a batch. */
 typedef struct {
     uint32_t automaton; /* index into the automata array */

@@ -28,7 +28,7 @@ AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL = 0, 1, 2, 3
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
-    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_batch", "ac_result_free", "ac_serve_create", "ac_serve_submit",
+    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_result_free", "ac_serve_create", "ac_serve_submit",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
     "ac_version",
 )
@@ -110,6 +110,7 @@ def _declare(lib):
         "ac_scan_keys_async": (C.c_int, [vp, vp, u64, C.c_int, vp, vp, u64, vp, vp]),
         "ac_key_shift": (C.c_int, [vp]),
         "ac_sort_keys_async": (C.c_int, [vp, u64, vp, vp, u64, vp, vp, vp]),
+        "ac_scan_noalloc": (C.c_int, [vp, vp, u64, C.c_int, vp, vp, u64, vp, vp]),
         "ac_scan_batch": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_batch_item), u32, C.c_int, vp,
                                     C.POINTER(ac_result)]),
         "ac_result_free": (None, [C.POINTER(ac_result)]),
@@ -332,6 +333,16 @@ def ac_sort_keys_async(a: Automaton, n: int, d_keys, d_num, cap: int, stream, d_
                                   _stream_ptr(stream), _device_ptr(d_matches) if cap else None,
                                   _device_ptr(d_num_out))
     _check(rc, "ac_sort_keys_async")
+
+
+def ac_scan_noalloc(a: Automaton, d_text, n: int, fmt: int, stream, d_matches, cap: int, d_num, d_counts=None):
+    """Like :func:`ac_scan_async`, but the library allocates nothing: its
+    scratch is a fixed array built into the library (cap <= 262,144; texts
+    over 64 KiB must be 16-byte aligned; overlapping calls race)."""
+    rc = lib().ac_scan_noalloc(a.h, _device_ptr(d_text), int(n), fmt, _stream_ptr(stream),
+                               _device_ptr(d_matches) if cap else None, int(cap), _device_ptr(d_num),
+                               _device_ptr(d_counts) if d_counts is not None else None)
+    _check(rc, "ac_scan_noalloc")
 
 
 def ac_scan_batch(automata, items, mem: int = AC_HOST, stream=None):
