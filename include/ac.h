@@ -241,12 +241,32 @@ typedef struct {
     uint64_t n;         /* symbols */
 } ac_batch_item;
 
-/* Scan ni texts, each against one of na resident automata, in one persistent
- * launch (replayed from a CUDA graph when the same batch shape recurs).
- * mem = AC_HOST or AC_DEVICE for all item texts. outs[i] receives item i's
- * result (counts sized by its automaton's pattern count). Synchronous. */
+/* Flags of ac_scan_batch. */
+#define AC_BATCH_NO_COUNTS 1u /* leave outs[i].counts NULL (no per-text count arrays) */
+#define AC_BATCH_GRAPH 2u     /* keep this batch's plan (layout, device buffers, autotuned row length and
+                                 CTA shape) and replay it as one CUDA graph when the same batch -- same
+                                 automata, same text pointers, lengths and formats -- is scanned again; the
+                                 first such call autotunes. At most two plans are kept; ac_batch_release
+                                 drops them. */
+
+/* Scan ni texts, each against one of na resident automata (all built on the
+ * same device), in one persistent launch per alphabet class: the texts are
+ * laid out in one device arena of whole chain rows, grouped by automaton, and
+ * a tile list assigns (automaton subset, rows) pairs to persistent CTAs
+ * (Section III's input- and pattern-focused splits applied to many texts at
+ * once). mem = AC_HOST or AC_DEVICE for all item texts; texts are copied
+ * into the arena inside the call. outs[i] receives item i's sorted matches
+ * (positions relative to item i's text) and, unless AC_BATCH_NO_COUNTS, its
+ * counts (sized by its automaton's pattern count). Synchronous. Errors:
+ * AC_EINVAL (NULL, bad automaton index or format, automata on different
+ * devices), AC_ERANGE (a text of 2^32 symbols or more, a batch too large for
+ * one launch), AC_ENOMEM, AC_ECUDA, AC_ETIMEDOUT. On error every outs[i] is
+ * left zeroed. */
 AC_API int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const ac_batch_item *items,
-                  uint32_t ni, int mem, void *stream, ac_result *outs);
+                         uint32_t ni, int mem, uint32_t flags, void *stream, ac_result *outs);
+
+/* Drop the plans kept by AC_BATCH_GRAPH (their device and pinned memory). */
+AC_API void ac_batch_release(void);
 
 /* Release the arrays of a result (NULL or zeroed is a no-op). */
 AC_API void ac_result_free(ac_result *r);

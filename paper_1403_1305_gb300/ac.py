@@ -25,10 +25,11 @@ AC_OK, AC_EINVAL, AC_ENOMEM, AC_ERANGE, AC_ECUDA, AC_ETIMEDOUT, AC_EAGAIN, AC_EB
 AC_U8, AC_PACKED2 = 0, 1
 AC_HOST, AC_DEVICE = 0, 1
 AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL = 0, 1, 2, 3
+AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
-    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_result_free", "ac_serve_create", "ac_serve_submit",
+    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_serve_create", "ac_serve_submit",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
     "ac_version",
 )
@@ -111,8 +112,9 @@ def _declare(lib):
         "ac_key_shift": (C.c_int, [vp]),
         "ac_sort_keys_async": (C.c_int, [vp, u64, vp, vp, u64, vp, vp, vp]),
         "ac_scan_noalloc": (C.c_int, [vp, vp, u64, C.c_int, vp, vp, u64, vp, vp]),
-        "ac_scan_batch": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_batch_item), u32, C.c_int, vp,
+        "ac_scan_batch": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_batch_item), u32, C.c_int, u32, vp,
                                     C.POINTER(ac_result)]),
+        "ac_batch_release": (None, []),
         "ac_result_free": (None, [C.POINTER(ac_result)]),
         "ac_serve_create": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_serve_opts), C.POINTER(vp)]),
         "ac_serve_submit": (C.c_int, [vp, u32, vp, u64, C.c_int, C.POINTER(u64)]),
@@ -345,10 +347,10 @@ def ac_scan_noalloc(a: Automaton, d_text, n: int, fmt: int, stream, d_matches, c
     _check(rc, "ac_scan_noalloc")
 
 
-def ac_scan_batch(automata, items, mem: int = AC_HOST, stream=None):
+def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=None):
     """``items``: list of ``(automaton_index, text, n, fmt)``; texts are host
     buffers (mem=AC_HOST) or CUDA tensors (mem=AC_DEVICE). Returns a list of
-    ``(matches, counts)``."""
+    ``(matches, counts)`` (counts None with AC_BATCH_NO_COUNTS)."""
     hs = (C.c_void_p * max(1, len(automata)))(*[a.h for a in automata])
     arr = (ac_batch_item * max(1, len(items)))()
     keep = []
@@ -360,9 +362,17 @@ def ac_scan_batch(automata, items, mem: int = AC_HOST, stream=None):
             keep.append(k)
         arr[i] = ac_batch_item(int(ai), int(fmt), ptr, int(n))
     outs = (ac_result * max(1, len(items)))()
-    _check(lib().ac_scan_batch(hs, len(automata), arr, len(items), mem, _stream_ptr(stream), outs),
+    _check(lib().ac_scan_batch(hs, len(automata), arr, len(items), mem, int(flags), _stream_ptr(stream), outs),
            "ac_scan_batch")
-    return [_result_to_numpy(outs[i]) for i in range(len(items))]
+    res = []
+    for i in range(len(items)):
+        m, c = _result_to_numpy(outs[i])
+        res.append((m, None if flags & AC_BATCH_NO_COUNTS else c))
+    return res
+
+
+def ac_batch_release():
+    lib().ac_batch_release()
 
 
 # ---------------------------------------------------------------- serving

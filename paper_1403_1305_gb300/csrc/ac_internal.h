@@ -39,6 +39,21 @@ struct SubsetDev {
     uint32_t id_lo;
 };
 
+// One text of a batch, laid out from row `row_begin` of the arena.
+struct BatchItemDev {
+    uint64_t row_begin;  // first arena row
+    uint64_t rows;       // rows it occupies
+    uint64_t nsym;       // symbols
+    uint64_t vbase;      // arena position of its first symbol (key position base)
+    uint64_t cbase;      // offset of its counts in the counts array
+};
+
+struct BatchTileDev {
+    uint32_t machine;    // index into the machine (subset) descriptors
+    uint32_t pad;
+    uint64_t row0;       // first arena row of the tile
+};
+
 struct DeviceSubset {
     uint32_t *table = nullptr, *out_off = nullptr, *out_ids = nullptr;
 };
@@ -96,6 +111,32 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
                 cudaStream_t stream);
+
+// Several texts laid out in one arena of whole rows (ac_scan_batch, serving).
+struct BatchLaunch {
+    const uint8_t *arena;        // 16-byte aligned; rows * row_bytes bytes readable
+    uint64_t rows;
+    uint32_t row_bytes;          // multiple of kStageBytes
+    int fmt;
+    const BatchItemDev *items;   // device, sorted by row_begin
+    uint32_t num_items;
+    const BatchTileDev *tiles;   // device
+    uint64_t num_tiles;
+    const SubsetDev *machines;   // device, one per (automaton, subset)
+    uint32_t max_states;         // over the machines
+    uint32_t sigma;              // common to every automaton of the launch
+    const uint8_t *sym_of_byte;  // 256 entries, common
+    bool acgt;
+    uint32_t key_shift;
+    int placement;
+    uint32_t smem_cap_bytes;
+    int device;
+    ac_scan_config cfg;          // threads and chains (row length is row_bytes)
+};
+int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t stream);
+// shared-memory plan of a launch: table rows held in shared memory and the dynamic size
+int plan_smem(int device, const ac_scan_config &cfg, uint32_t sigma, int placement, uint32_t smem_cap,
+              uint32_t max_states, uint32_t *rows_used, bool *hybrid, size_t *smem_bytes, uint32_t *table_words);
 int launch_fill_u64(unsigned long long *p, uint64_t count, unsigned long long value, cudaStream_t stream);
 int launch_keys_to_matches(const unsigned long long *keys, const unsigned long long *num, uint64_t cap,
                            uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,

@@ -8,16 +8,6 @@ int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *s
     if (chosen) *chosen = a->cfg;
     return AC_OK;
 }
-int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const ac_batch_item *items, uint32_t ni, int mem,
-                  void *stream, ac_result *outs) {
-    if (!as || !items || !outs) return set_error(AC_EINVAL, "ac_scan_batch: NULL");
-    for (uint32_t i = 0; i < ni; ++i) {
-        if (items[i].automaton >= na) return set_error(AC_EINVAL, "ac_scan_batch: bad automaton index");
-        int rc = ac_scan(as[items[i].automaton], items[i].text, items[i].n, items[i].fmt, mem, stream, &outs[i]);
-        if (rc) { for (uint32_t j = 0; j < i; ++j) ac_result_free(&outs[j]); return rc; }
-    }
-    return AC_OK;
-}
 int ac_serve_create(const ac_automaton *const *, uint32_t, const ac_serve_opts *, ac_server **) { return set_error(AC_EINVAL, "serving not built"); }
 int ac_serve_submit(ac_server *, uint32_t, const uint8_t *, uint64_t, int, uint64_t *) { return AC_EINVAL; }
 int ac_serve_poll(ac_server *, uint64_t, ac_result *) { return AC_EINVAL; }

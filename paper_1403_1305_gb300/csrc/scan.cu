@@ -52,6 +52,14 @@ enum { FMT_U8 = 0, FMT_P2 = 1 };
 enum { ALPHA_MAP = 0, ALPHA_ACGT = 1 };
 enum { MODE_SMEM = 0, MODE_HYBRID = 1 };
 
+// What a chain needs to know about the text its row belongs to.
+struct ChainText {
+    uint64_t row_in_text;  // row index within its text
+    uint64_t nsym;         // symbols of its text
+    uint64_t vbase;        // key position of the text's first symbol
+    uint64_t cbase;        // counts offset of the text
+};
+
 struct ScanParams {
     const uint8_t *text;
     uint64_t nbytes;        // bytes of text
@@ -73,6 +81,10 @@ struct ScanParams {
     unsigned long long *num;
     unsigned long long *counts;
     uint32_t *err;
+    // batch mode (several texts in one arena of whole rows)
+    const BatchItemDev *items;  // sorted by first row
+    const BatchTileDev *tiles;  // one per tile: machine and first row
+    uint32_t num_items;
     uint8_t sym_of_byte[256];
 };
 
@@ -174,8 +186,8 @@ __device__ __forceinline__ uint32_t lookup4(const uint32_t *__restrict__ stab, c
 
 // Emit the output of state `sid` at position `pos` for every lane with
 // `has`; all 32 lanes must call this together.
-__device__ __forceinline__ void emit_warp(bool has, uint32_t sid, uint64_t pos, const SubsetDev &sd,
-                                          const ScanParams &p, uint32_t lane) {
+__device__ __forceinline__ void emit_warp(bool has, uint32_t sid, uint64_t pos, uint64_t cbase,
+                                          const SubsetDev &sd, const ScanParams &p, uint32_t lane) {
     unsigned m = __ballot_sync(kFull, has);
     if (m == 0) return;
     uint32_t b = 0, cnt = 0;
@@ -197,7 +209,7 @@ __device__ __forceinline__ void emit_warp(bool has, uint32_t sid, uint64_t pos, 
     for (uint32_t t = 0; t < cnt; ++t) {
         uint32_t id = __ldg(sd.out_ids + b + t);
         if (slot + t < p.cap) p.keys[slot + t] = (pos << p.key_shift) | id;
-        if (p.counts) atomicAdd(p.counts + id, 1ull);
+        if (p.counts) atomicAdd(p.counts + cbase + id, 1ull);
     }
 }
 
@@ -213,15 +225,15 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &w, int e) {
 // lanes call it together; returns the state after the stage.
 template <int FMT>
 __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool active, bool main_stage,
-                                             const uint4 w0, const uint4 w1, const ScanParams &p,
-                                             const SubsetDev &sd, const uint32_t *stab, const uint8_t *smap,
-                                             uint32_t hot, uint32_t lane) {
+                                             const uint4 w0, const uint4 w1, const ChainText &ct,
+                                             const ScanParams &p, const SubsetDev &sd, const uint32_t *stab,
+                                             const uint8_t *smap, uint32_t hot, uint32_t lane) {
     constexpr uint32_t SYM = (FMT == FMT_U8) ? kStageBytes : kStageBytes * 4;
     const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     uint32_t sc = s_in;
     for (uint32_t i = 0; i < SYM; ++i) {
         const int64_t pos = pos0 + i;
-        const bool live = active && pos >= 0 && pos < (int64_t)p.nsym;
+        const bool live = active && pos >= 0 && pos < (int64_t)ct.nsym;
         bool has = false;
         if (live) {
             const uint32_t bi = (FMT == FMT_U8) ? i : (i >> 2);
@@ -234,7 +246,7 @@ __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool 
         } else if (pos < 0) {
             sc = 0;
         }
-        emit_warp(has, sc, (uint64_t)(pos < 0 ? 0 : pos), sd, p, lane);
+        emit_warp(has, sc, ct.vbase + (uint64_t)(pos < 0 ? 0 : pos), ct.cbase, sd, p, lane);
     }
     return sc;
 }
@@ -245,7 +257,34 @@ __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool 
 // for the ragged last row (written by a 1-D TMA), padded to 128 bytes.
 __host__ __device__ constexpr uint32_t slot_bytes_for(uint32_t C) { return C * 1024u + 128u; }
 
-template <int FMT, int ALPHA, int MODE, int C>
+// The chain's text: in single-text mode the row index is the text row; in
+// batch mode the row's text is found by binary search over the items.
+template <bool BATCH>
+__device__ __forceinline__ bool chain_text(uint64_t row, const ScanParams &p, ChainText &ct) {
+    if (!BATCH) {
+        ct.row_in_text = row;
+        ct.nsym = p.nsym;
+        ct.vbase = 0;
+        ct.cbase = 0;
+        return row < p.num_rows;
+    }
+    uint32_t lo = 0, hi = p.num_items;  // first item whose row_begin > row
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (p.items[mid].row_begin <= row) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo == 0) return false;
+    const BatchItemDev it = p.items[lo - 1];
+    if (row >= it.row_begin + it.rows) return false;
+    ct.row_in_text = row - it.row_begin;
+    ct.nsym = it.nsym;
+    ct.vbase = it.vbase;
+    ct.cbase = it.cbase;
+    return true;
+}
+
+template <int FMT, int ALPHA, int MODE, int C, bool BATCH>
 __global__ void __launch_bounds__(512, 1)
     scan_kernel(const __grid_constant__ ScanParams p, const __grid_constant__ CUtensorMap rows_map,
                 const __grid_constant__ CUtensorMap tail_map) {
@@ -276,8 +315,16 @@ __global__ void __launch_bounds__(512, 1)
     const int64_t L = p.row_bytes;
 
     for (uint64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-        const uint32_t k = (uint32_t)(tile % p.K);
-        const uint64_t rb = tile / p.K;
+        uint32_t k;
+        uint64_t tile_row0;
+        if (BATCH) {
+            const BatchTileDev td = p.tiles[tile];
+            k = td.machine;
+            tile_row0 = td.row0;
+        } else {
+            k = (uint32_t)(tile % p.K);
+            tile_row0 = (tile / p.K) * p.rows_per_tile;
+        }
         const SubsetDev sd = p.subs[k];
         const uint32_t hot = min(sd.states, p.smem_rows);
         if ((int)k != cur_k) {
@@ -295,9 +342,9 @@ __global__ void __launch_bounds__(512, 1)
         const uint32_t warm_bytes = (FMT == FMT_U8) ? sd.warm : (sd.warm + 3) / 4;
         const uint32_t nW = (warm_bytes + BX - 1) / BX;
         const uint32_t nst = nW + p.row_bytes / BX;
-        const uint64_t row0 = rb * p.rows_per_tile + (uint64_t)warp * 32 * C;
+        const uint64_t row0 = tile_row0 + (uint64_t)warp * 32 * C;
         if (row0 >= p.num_rows) continue;
-        const bool tail_in_warp = p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
+        const bool tail_in_warp = !BATCH && p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
 
         // lane 0 issues one 2-D box per chain group (and the tail row's 1-D box)
         auto issue = [&](uint32_t s) {
@@ -327,10 +374,11 @@ __global__ void __launch_bounds__(512, 1)
         uint64_t row[C];
         bool active[C];
         uint32_t st8[C];
+        ChainText ct[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             row[j] = row0 + (uint64_t)j * 32 + lane;
-            active[j] = row[j] < p.num_rows;
+            active[j] = chain_text<BATCH>(row[j], p, ct[j]);
             st8[j] = 0;
         }
 
@@ -366,11 +414,11 @@ __global__ void __launch_bounds__(512, 1)
             uint32_t v[C], acc[C], bad[C], s_in[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const int64_t b0 = (int64_t)row[j] * L + o;
+                const int64_t b0 = (int64_t)ct[j].row_in_text * L + o;
                 pos0[j] = (FMT == FMT_U8) ? b0 : b0 * 4;
-                dead[j] = !active[j] || pos0[j] >= (int64_t)p.nsym;
+                dead[j] = !active[j] || pos0[j] >= (int64_t)ct[j].nsym;
                 before[j] = !dead[j] && pos0[j] + (int64_t)SYM_PER_STAGE <= 0;
-                fast[j] = !dead[j] && pos0[j] >= 0 && pos0[j] + (int64_t)SYM_PER_STAGE <= (int64_t)p.nsym;
+                fast[j] = !dead[j] && pos0[j] >= 0 && pos0[j] + (int64_t)SYM_PER_STAGE <= (int64_t)ct[j].nsym;
                 s_in[j] = st8[j];
                 v[j] = s_in[j];
                 acc[j] = 0;
@@ -436,7 +484,7 @@ __global__ void __launch_bounds__(512, 1)
             for (int j = 0; j < C; ++j) {
                 if (__any_sync(kFull, need[j])) {
                     const uint32_t sc = careful_walk<FMT>(s_in[j], pos0[j], active[j], main_stage, data[j][0],
-                                                          data[j][1], p, sd, stab, smap, hot, lane);
+                                                          data[j][1], ct[j], p, sd, stab, smap, hot, lane);
                     if (!dead[j]) st8[j] = sc;
                 }
             }
@@ -489,21 +537,28 @@ __global__ void mark_error_kernel(unsigned long long *num, const uint32_t *err) 
 // ------------------------------------------------------------------ dispatch
 using KernelFn = void (*)(ScanParams, CUtensorMap, CUtensorMap);
 
-template <int FMT, int ALPHA, int MODE>
+template <int FMT, int ALPHA, int MODE, bool BATCH>
 KernelFn pick_c(uint32_t C) {
     switch (C) {
-        case 1: return scan_kernel<FMT, ALPHA, MODE, 1>;
-        case 2: return scan_kernel<FMT, ALPHA, MODE, 2>;
-        default: return scan_kernel<FMT, ALPHA, MODE, 4>;
+        case 1: return scan_kernel<FMT, ALPHA, MODE, 1, BATCH>;
+        case 2: return scan_kernel<FMT, ALPHA, MODE, 2, BATCH>;
+        default: return scan_kernel<FMT, ALPHA, MODE, 4, BATCH>;
     }
 }
 
-KernelFn pick_kernel(int fmt, bool acgt, bool hybrid, uint32_t C) {
+template <bool BATCH>
+KernelFn pick_mode(int fmt, bool acgt, bool hybrid, uint32_t C) {
     if (fmt == AC_PACKED2)
-        return hybrid ? pick_c<FMT_P2, ALPHA_MAP, MODE_HYBRID>(C) : pick_c<FMT_P2, ALPHA_MAP, MODE_SMEM>(C);
+        return hybrid ? pick_c<FMT_P2, ALPHA_MAP, MODE_HYBRID, BATCH>(C)
+                      : pick_c<FMT_P2, ALPHA_MAP, MODE_SMEM, BATCH>(C);
     if (acgt)
-        return hybrid ? pick_c<FMT_U8, ALPHA_ACGT, MODE_HYBRID>(C) : pick_c<FMT_U8, ALPHA_ACGT, MODE_SMEM>(C);
-    return hybrid ? pick_c<FMT_U8, ALPHA_MAP, MODE_HYBRID>(C) : pick_c<FMT_U8, ALPHA_MAP, MODE_SMEM>(C);
+        return hybrid ? pick_c<FMT_U8, ALPHA_ACGT, MODE_HYBRID, BATCH>(C)
+                      : pick_c<FMT_U8, ALPHA_ACGT, MODE_SMEM, BATCH>(C);
+    return hybrid ? pick_c<FMT_U8, ALPHA_MAP, MODE_HYBRID, BATCH>(C) : pick_c<FMT_U8, ALPHA_MAP, MODE_SMEM, BATCH>(C);
+}
+
+KernelFn pick_kernel(int fmt, bool acgt, bool hybrid, uint32_t C, bool batch) {
+    return batch ? pick_mode<true>(fmt, acgt, hybrid, C) : pick_mode<false>(fmt, acgt, hybrid, C);
 }
 
 uint32_t bits_for(uint64_t x) {  // bits needed to hold values 0..x
@@ -592,6 +647,83 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
 
 int key_shift_for(const ac_automaton *a) { return (int)bits_for(a->P ? a->P - 1 : 0); }
 
+int plan_smem(int device, const ac_scan_config &cfg, uint32_t sigma, int placement, uint32_t smem_cap,
+              uint32_t max_states, uint32_t *rows_used, bool *hybrid, size_t *smem_bytes, uint32_t *table_words) {
+    // shared memory: table prefix (rounded to 128 bytes) + map + staging + barriers
+    const int limit = scan_smem_limit(device);
+    const uint32_t staging = scan_stage_bytes_per_cta(cfg);
+    if ((int)staging + 1024 > limit) return set_error(AC_EINVAL, "scan: staging does not fit in shared memory");
+    uint64_t avail = (uint64_t)limit - staging - 128;
+    if (smem_cap && smem_cap < avail) avail = smem_cap;
+    uint32_t rows_fit = (uint32_t)(avail / (4ull * sigma));
+    if (placement == AC_PLACE_GLOBAL) rows_fit = 0;
+    *hybrid = max_states > rows_fit;
+    if (placement == AC_PLACE_SMEM && *hybrid)
+        return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory (%u rows)", max_states,
+                         rows_fit);
+    *rows_used = std::min(max_states, rows_fit);
+    *table_words = (*rows_used * sigma + 3) & ~3u;
+    *smem_bytes = (((size_t)*table_words * 4 + 127) & ~(size_t)127) + staging;
+    if (*smem_bytes > (size_t)limit) return set_error(AC_EINVAL, "scan: shared memory plan exceeds the limit");
+    return AC_OK;
+}
+
+int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t stream) {
+    const ac_scan_config &cfg = b.cfg;
+    if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32 || (cfg.chains != 1 && cfg.chains != 2 &&
+                                                                        cfg.chains != 4))
+        return set_error(AC_EINVAL, "batch: bad threads/chains");
+    if (b.num_tiles == 0) return AC_OK;
+    if (b.row_bytes % kStageBytes || ((uintptr_t)b.arena & 15))
+        return set_error(AC_EINVAL, "batch: arena rows must be 32-byte multiples at a 16-byte aligned address");
+    ScanParams p{};
+    p.text = b.arena;
+    p.nbytes = b.rows * b.row_bytes;
+    p.nsym = 0;
+    p.full_rows = b.rows;
+    p.num_rows = b.rows;
+    p.num_tiles = b.num_tiles;
+    p.row_bytes = b.row_bytes;
+    p.rows_per_tile = cfg.threads * cfg.chains;
+    p.K = 1;
+    p.sigma = b.sigma;
+    p.subs = b.machines;
+    p.keys = o.keys;
+    p.cap = o.cap;
+    p.num = o.num;
+    p.counts = o.counts;
+    p.err = o.err;
+    p.key_shift = b.key_shift;
+    p.tail_bytes = 0;
+    p.items = b.items;
+    p.tiles = b.tiles;
+    p.num_items = b.num_items;
+    memcpy(p.sym_of_byte, b.sym_of_byte, 256);
+    if (b.rows >= (1ull << 31)) return set_error(AC_ERANGE, "batch: arena too large for one launch");
+    CUtensorMap rows_map, tail_map;
+    memset(&tail_map, 0, sizeof(tail_map));
+    int rc = encode_rows_map(&rows_map, b.arena, b.row_bytes, b.rows);
+    if (rc) return rc;
+    uint32_t rows_used = 0;
+    bool hybrid = false;
+    size_t smem = 0;
+    rc = plan_smem(b.device, cfg, b.sigma, b.placement, b.smem_cap_bytes, b.max_states, &rows_used, &hybrid, &smem,
+                   &p.table_words);
+    if (rc) return rc;
+    p.smem_rows = rows_used;
+    KernelFn fn = pick_kernel(b.fmt, b.fmt == AC_U8 && b.acgt, hybrid, cfg.chains, true);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "batch: %s", cudaGetErrorString(e));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device);
+    uint64_t grid = cfg.ctas ? cfg.ctas : (uint64_t)sms;
+    if (grid > b.num_tiles) grid = b.num_tiles;
+    fn<<<(unsigned)grid, cfg.threads, smem, stream>>>(p, rows_map, tail_map);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg_in,
                 cudaStream_t stream) {
     ac_scan_config cfg = cfg_in;
@@ -647,28 +779,18 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
         if (rc) return rc;
     }
 
-    // shared memory: table prefix + map + staging + barriers
-    const int limit = scan_smem_limit(a->device);
-    const uint32_t staging = scan_stage_bytes_per_cta(cfg);
-    if ((int)staging + 1024 > limit) return set_error(AC_EINVAL, "scan: staging does not fit in shared memory");
-    uint64_t avail = (uint64_t)limit - staging - 128;  // the table is rounded up to 128 bytes
-    if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
-    uint32_t rows_fit = (uint32_t)(avail / (4ull * a->sigma));
-    if (a->placement == AC_PLACE_GLOBAL) rows_fit = 0;
     uint32_t max_states = 0;
     for (auto &d : a->h_desc) max_states = std::max(max_states, d.states);
-    const bool hybrid = max_states > rows_fit;
-    if (a->placement == AC_PLACE_SMEM && hybrid)
-        return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory (%u rows)", max_states,
-                         rows_fit);
-    const uint32_t rows_used = std::min(max_states, rows_fit);
+    uint32_t rows_used = 0;
+    bool hybrid = false;
+    size_t smem = 0;
+    rc = plan_smem(a->device, cfg, a->sigma, a->placement, a->smem_cap_bytes, max_states, &rows_used, &hybrid, &smem,
+                   &p.table_words);
+    if (rc) return rc;
     p.smem_rows = rows_used;
-    p.table_words = (rows_used * a->sigma + 3) & ~3u;
-    const size_t smem = (((size_t)p.table_words * 4 + 127) & ~(size_t)127) + staging;
-    if (smem > (size_t)limit) return set_error(AC_EINVAL, "scan: shared memory plan exceeds the limit");
 
     const bool acgt = t.fmt == AC_U8 && a->dna_acgt;
-    KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, cfg.chains);
+    KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, cfg.chains, false);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
     int sms = 148;
