@@ -84,6 +84,8 @@ __global__ void batch_offsets_kernel(const unsigned long long *__restrict__ keys
 
 struct Plan {
     int device = 0, fmt = AC_U8, mem = AC_HOST;
+    cudaStream_t pool_stream = nullptr;  // transient plans: buffers from the stream-ordered pool
+    bool pooled = false;
     uint32_t flags = 0;
     std::vector<uint32_t> caller;        // plan order -> caller's item index
     std::vector<const uint8_t *> src;    // plan order -> text
@@ -121,7 +123,10 @@ void free_plan_buffers(Plan &P) {
     void *dev[] = {P.d_arena, P.d_items, P.d_tiles, P.d_machines, P.d_num, P.d_keys, P.d_alt,
                    P.d_counts, P.d_off, P.d_rec, P.d_sort};
     for (void *p : dev)
-        if (p) cudaFree(p);
+        if (p) {
+            if (P.pooled) dev_free(p, P.pool_stream);
+            else cudaFree(p);
+        }
     void *host[] = {P.h_stage, P.h_rec, P.h_off, P.h_counts, P.h_num};
     for (void *p : host)
         if (p) cudaFreeHost(p);
@@ -214,7 +219,11 @@ uint32_t default_row_bytes(uint64_t total_bytes, uint32_t max_warm_bytes, const 
     return (uint32_t)((L + kStageBytes - 1) / kStageBytes * kStageBytes);
 }
 
-int alloc_dev(void **p, size_t bytes) {
+int alloc_dev(void **p, size_t bytes, const Plan &P) {
+    if (P.pooled) {
+        *p = dev_alloc(bytes ? bytes : 16, P.pool_stream);
+        return *p ? AC_OK : set_error(AC_ENOMEM, "ac_scan_batch: device memory (%zu bytes)", bytes);
+    }
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -240,21 +249,33 @@ int alloc_plan(Plan &P, uint64_t cap) {
     P.cap = cap;
     const uint32_t ni = (uint32_t)P.items.size();
     int rc;
-    if ((rc = alloc_dev((void **)&P.d_arena, P.arena_bytes()))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_items, ni * sizeof(BatchItemDev)))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_tiles, P.tiles.size() * sizeof(BatchTileDev)))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_machines, P.machines.size() * sizeof(SubsetDev)))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_num, 16))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_keys, cap * 8))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_alt, cap * 8))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_rec, cap * 8))) return rc;
-    if ((rc = alloc_dev((void **)&P.d_off, (ni + 1) * 8))) return rc;
-    if (P.total_counts && (rc = alloc_dev((void **)&P.d_counts, P.total_counts * 8))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_arena, P.arena_bytes(), P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_items, ni * sizeof(BatchItemDev), P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_tiles, P.tiles.size() * sizeof(BatchTileDev), P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_machines, P.machines.size() * sizeof(SubsetDev), P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_num, 16, P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_keys, cap * 8, P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_alt, cap * 8, P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_rec, cap * 8, P))) return rc;
+    if ((rc = alloc_dev((void **)&P.d_off, (ni + 1) * 8, P))) return rc;
+    if (P.total_counts && (rc = alloc_dev((void **)&P.d_counts, P.total_counts * 8, P))) return rc;
     const int end_bit = (int)std::min<uint32_t>(64, P.key_shift + value_bits(P.rows * P.row_bytes * 4));
     P.sort_bytes = 0;
     cub::DoubleBuffer<unsigned long long> db(P.d_keys, P.d_alt);
     BCK(cub::DeviceRadixSort::SortKeys(nullptr, P.sort_bytes, db, (int)cap, 0, end_bit), "ac_scan_batch: sort size");
-    if ((rc = alloc_dev(&P.d_sort, P.sort_bytes))) return rc;
+    if ((rc = alloc_dev(&P.d_sort, P.sort_bytes, P))) return rc;
+    if (P.pooled) {
+        cudaStream_t s = P.pool_stream;
+        BCK(cudaMemcpyAsync(P.d_items, P.items.data(), ni * sizeof(BatchItemDev), cudaMemcpyHostToDevice, s),
+            "ac_scan_batch");
+        BCK(cudaMemcpyAsync(P.d_tiles, P.tiles.data(), P.tiles.size() * sizeof(BatchTileDev), cudaMemcpyHostToDevice,
+                            s),
+            "ac_scan_batch");
+        BCK(cudaMemcpyAsync(P.d_machines, P.machines.data(), P.machines.size() * sizeof(SubsetDev),
+                            cudaMemcpyHostToDevice, s),
+            "ac_scan_batch");
+        return AC_OK;
+    }
     BCK(cudaMemcpy(P.d_items, P.items.data(), ni * sizeof(BatchItemDev), cudaMemcpyHostToDevice), "ac_scan_batch");
     BCK(cudaMemcpy(P.d_tiles, P.tiles.data(), P.tiles.size() * sizeof(BatchTileDev), cudaMemcpyHostToDevice),
         "ac_scan_batch");
@@ -497,6 +518,8 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
         if (!(flags & AC_BATCH_GRAPH)) {
             Plan P;
             init_plan(P);
+            P.pooled = true;
+            P.pool_stream = s;
             const uint32_t L = rep->cfg.row_len ? (uint32_t)((rep->cfg.row_len / (fmt == AC_U8 ? 1 : 4) + 31) / 32 * 32)
                                                 : default_row_bytes(total, warm, cfg, device);
             rc = layout(as, items, idx, std::max<uint32_t>(L, kStageBytes), cfg, flags, P);
@@ -505,7 +528,6 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
                 rc = alloc_plan(P, cap);
                 uint64_t M = 0;
                 if (rc == AC_OK) rc = run_once(P, s, outs, &M);
-                cudaStreamSynchronize(s);
                 free_plan_buffers(P);
                 if (rc != AC_OK || M <= cap) break;
                 cap = M;
@@ -637,6 +659,8 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
             for (uint32_t i : idx) ac_result_free(&outs[i]);
             Plan Q;
             init_plan(Q);
+            Q.pooled = true;
+            Q.pool_stream = s;
             rc = layout(as, items, idx, P->row_bytes, P->cfg, flags, Q);
             if (rc == AC_OK) rc = alloc_plan(Q, M);
             if (rc == AC_OK) rc = run_once(Q, s, outs, &M);

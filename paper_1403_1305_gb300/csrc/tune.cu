@@ -1,0 +1,68 @@
+// ac_tune: pick the scan configuration (row length, threads per CTA, chains
+// per thread) for an automaton by timing candidates on a real text.
+#include "ac_internal.h"
+
+using namespace acgb;
+
+extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
+                       ac_scan_config *chosen) {
+    if (!a || (!d_text && n)) return set_error(AC_EINVAL, "ac_tune: NULL argument");
+    if (a->device < 0) return set_error(AC_EINVAL, "ac_tune: host-only automaton");
+    if (fmt != AC_U8 && fmt != AC_PACKED2) return set_error(AC_EINVAL, "ac_tune: unknown format");
+    if (fmt == AC_PACKED2 && a->sigma != 4) return set_error(AC_EINVAL, "ac_tune: packed text needs 4 letters");
+    const uint64_t nbytes = fmt == AC_U8 ? n : (n + 3) / 4;
+    if (nbytes < 64 || ((uintptr_t)d_text & 15))
+        return set_error(AC_EINVAL, "ac_tune: the text must be 16-byte aligned and at least 64 bytes");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != a->device) cudaSetDevice(a->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t cap = n / 256 + 4096;
+    unsigned long long *num = (unsigned long long *)dev_alloc(16, s);
+    unsigned long long *keys = (unsigned long long *)dev_alloc(cap * 8, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const ac_scan_config saved = a->cfg;
+    ac_scan_config best{};
+    float best_ms = 1e30f;
+    int rc = (num && keys) ? AC_OK : set_error(AC_ENOMEM, "ac_tune: scratch");
+    const uint32_t threads[2] = {256, 512}, chains[3] = {1, 2, 4};
+    for (int ti = 0; ti < 2 && rc == AC_OK; ++ti)
+        for (int ci = 0; ci < 3 && rc == AC_OK; ++ci)
+            for (int li = 0; li < 3 && rc == AC_OK; ++li) {
+                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0};
+                ac_scan_config c;
+                default_config(a, n, fmt, &c);
+                c.row_len = li == 0 ? std::max<uint32_t>(64, c.row_len / 2) : li == 1 ? c.row_len : c.row_len * 2;
+                ScanText t{d_text, n, fmt, nbytes};
+                ScanOut o{keys, cap, num, nullptr, (uint32_t *)(num + 1)};
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaMemsetAsync(num, 0, 16, s);
+                    cudaEventRecord(e0, s);
+                    if (launch_scan(a, t, o, c, s) != AC_OK) break;
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc = set_error(AC_ECUDA, "ac_tune: %s", cudaGetErrorString(cudaGetLastError()));
+                        break;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms_best = std::min(ms_best, ms);
+                }
+                if (ms_best < best_ms) {
+                    best_ms = ms_best;
+                    best = c;
+                }
+            }
+    cudaGetLastError();  // a candidate that did not fit (shared memory) is skipped
+    a->cfg = (rc == AC_OK && best_ms < 1e29f) ? best : saved;
+    if (chosen) *chosen = a->cfg;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(keys, s);
+    dev_free(num, s);
+    if (prev >= 0 && prev != a->device) cudaSetDevice(prev);
+    return rc;
+}
