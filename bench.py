@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-texts", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -280,6 +284,155 @@ def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
     return total, scan, M
 
 
+def bench_batch(A, torch, dev, args):
+    """4,096 DNA texts (log-uniform 1 KiB..4 MiB) against 8 resident pattern
+    sets: one ac_scan_batch (kept plan replayed as a CUDA graph) against one
+    ac_scan_async call per text, texts resident on the device in both."""
+    w = workloads.config4(num_texts=args.batch_texts)
+    autos = [A.ac_build(s, alphabet="ACGT", device=dev) for s in w.pattern_sets]
+    d_texts = [torch.from_numpy(t).to(f"cuda:{dev}") for t in w.texts]
+    total = int(sum(t.size for t in w.texts))
+    items = [(int(a), d, t.size, A.AC_U8) for a, d, t in zip(w.set_of_text, d_texts, w.texts)]
+    torch.cuda.synchronize()
+    # plan + autotune, then timed graph replays (results copied to the host and split per text)
+    fl = A.AC_BATCH_GRAPH | A.AC_BATCH_NO_COUNTS
+    t0 = time.perf_counter()
+    res = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fl)
+    plan_s = time.perf_counter() - t0
+    A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fl)
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        res = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fl)
+    batched_s = (time.perf_counter() - t0) / reps
+    M = sum(m.shape[0] for m, _ in res)
+    # the same with per-text dense count arrays copied to the host as well
+    A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH)
+    t0 = time.perf_counter()
+    A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH)
+    counts_s = time.perf_counter() - t0
+    # one launch sequence per text: ac_scan_async on one stream, one sync at the end
+    stream = torch.cuda.Stream()
+    caps = [max(4096, t.size // 512) for t in w.texts]
+    d_m = torch.empty(max(caps), dtype=torch.int64, device=f"cuda:{dev}")
+    d_num = torch.zeros(len(items), dtype=torch.int64, device=f"cuda:{dev}")
+    d_c = torch.empty(max(a.num_patterns for a in autos), dtype=torch.int64, device=f"cuda:{dev}")
+
+    def per_call():
+        with torch.cuda.stream(stream):
+            for i, (ai, d, n, f) in enumerate(items):
+                A.ac_scan_async(autos[ai], d, n, f, stream, d_m, caps[i], d_num[i:i + 1], d_c[:autos[ai].num_patterns])
+        stream.synchronize()
+
+    per_call()
+    t0 = time.perf_counter()
+    per_call()
+    per_call_s = time.perf_counter() - t0
+    M_calls = int(d_num.sum().item())
+    A.ac_batch_release()
+    return {"workload": w.name, "texts": len(items), "text_bytes": total, "pattern_sets": w.meta["set_sizes"],
+            "batched_GBps": total / batched_s / 1e9, "batched_ms": batched_s * 1e3,
+            "per_call_GBps": total / per_call_s / 1e9, "per_call_ms": per_call_s * 1e3,
+            "speedup": per_call_s / batched_s, "plan_and_autotune_ms": plan_s * 1e3,
+            "batched_with_counts_ms": counts_s * 1e3,
+            "count_array_bytes": int(sum(autos[int(a)].num_patterns for a in w.set_of_text) * 8),
+            "matches": M, "matches_per_call_path": M_calls,
+            "batched_path": "ac_scan_batch(AC_DEVICE, AC_BATCH_GRAPH|AC_BATCH_NO_COUNTS): arena copy + 1 "
+                            "persistent scan + sort + records, matches to the host per text",
+            "per_call_path": "ac_scan_async per text (device results), one stream"}
+
+
+def bench_serve(A, torch, dev, args):
+    """16 resident automata (8 DNA x 5,000, 8 protein x 20,000 patterns);
+    Poisson arrivals of texts with log-uniform lengths in [4 KiB, 64 MiB];
+    rate raised x1.5 until throughput stops growing. Continuous batching
+    server against one synchronous ac_scan per request in arrival order."""
+    w = workloads.config5_sets()
+    autos = [A.ac_build(s, alphabet=a, device=dev) for s, a in zip(w.pattern_sets, w.set_alphabet)]
+    rng = np.random.default_rng(1055)
+    # one 64 MiB text per alphabet kind; a protein set's text maps Zipf ranks
+    # through that set's letter order (same law as drawing it directly)
+    dna_pool = workloads.dna_text(rng, 64 << 20)
+    ranks = None
+    pools = []
+    for letters, probs in w.set_letters:
+        if probs is None:
+            pools.append(dna_pool)
+            continue
+        if ranks is None:
+            ranks = workloads.iid_text(rng, 64 << 20, np.arange(len(letters), dtype=np.uint8), probs)
+        pools.append(np.asarray(letters, dtype=np.uint8)[ranks])
+
+    def make(count, rate):
+        t, sets, lens = workloads.request_stream(rng, rate, count)
+        reqs = []
+        for ti, si, L in zip(t, sets, lens):
+            pool = pools[int(si)]
+            o = int(rng.integers(0, pool.size - int(L) + 1))
+            reqs.append((float(ti), int(si), pool[o:o + int(L)]))
+        return reqs
+
+    def run_server(reqs):
+        srv = A.ac_serve_create(autos, num_streams=3, max_batch_items=64, max_wait_us=100,
+                                device_mem_budget=8 << 30)
+        tickets = [None] * len(reqs)
+        start = time.perf_counter()
+
+        def producer():
+            for i, (ta, si, txt) in enumerate(reqs):
+                d = start + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = A.ac_serve_submit(srv, si, txt)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        for tk in tickets:
+            A.ac_serve_wait(srv, tk, 600_000)
+        end = time.perf_counter()
+        st = A.ac_serve_stats(srv)
+        A.ac_serve_destroy(srv)
+        return end - start, st
+
+    def run_per_request(reqs):
+        lat = []
+        start = time.perf_counter()
+        for ta, si, txt in reqs:
+            d = start + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            A.ac_scan(autos[si], txt)
+            lat.append((time.perf_counter() - start - ta) * 1e3)
+        return time.perf_counter() - start, lat
+
+    # raise the offered rate x1.5 until the server no longer keeps up with it
+    sweep, rate = [], 50.0
+    for _ in range(12):
+        reqs = make(args.serve_requests, rate)
+        nbytes = sum(r[2].size for r in reqs)
+        el, st = run_server(reqs)
+        thr = nbytes / el / 1e9
+        offered = len(reqs) / max(reqs[-1][0], 1e-9)
+        sweep.append({"rate_hz": rate, "GBps": thr, "req_per_s": len(reqs) / el, "offered_req_per_s": offered,
+                      "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_batch_items": st["mean_batch_items"],
+                      "launches": st["launches"]})
+        if len(reqs) / el < 0.85 * offered:
+            break
+        rate *= 1.5
+    top = max(sweep, key=lambda r: r["GBps"])
+    reqs = make(args.serve_requests, top["rate_hz"])
+    nbytes = sum(r[2].size for r in reqs)
+    el, lat = run_per_request(reqs)
+    return {"workload": w.name, "requests_per_rate": args.serve_requests, "sweep": sweep,
+            "served_GBps": top["GBps"], "served_p50_ms": top["p50_ms"], "served_p99_ms": top["p99_ms"],
+            "per_request_GBps": nbytes / el / 1e9, "per_request_p50_ms": float(np.percentile(lat, 50)),
+            "per_request_p99_ms": float(np.percentile(lat, 99)), "rate_hz_at_best": top["rate_hz"],
+            "speedup": top["GBps"] / (nbytes / el / 1e9),
+            "served_path": "ac_serve_* (3 streams, <=64 requests per launch, host texts)",
+            "per_request_path": "ac_scan(host text) per request in arrival order"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -380,6 +533,11 @@ def main():
                                 "smem_states": A.ac_stats(av)["smem_states"], "states": A.ac_stats(av)["states"]}
             del av, dt
         line["variants"] = var
+
+    if rank == 0 and not args.no_batch:
+        line["batch"] = bench_batch(A, torch, dev, args)
+    if rank == 0 and not args.no_serve:
+        line["serve"] = bench_serve(A, torch, dev, args)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
