@@ -138,10 +138,11 @@ typedef struct {
 
 /* Scan configuration (ac_set_scan_config / ac_tune). Zero fields = defaults. */
 typedef struct {
-    uint32_t row_len; /* text symbols per chain (rounded to the stage size) */
-    uint32_t threads; /* threads per CTA (multiple of 32, <= 1024) */
-    uint32_t chains;  /* independent chains per thread: 1, 2 or 4 */
-    uint32_t ctas;    /* persistent grid size; 0 = one per SM */
+    uint32_t row_len;     /* text symbols per chain (rounded up to 32 bytes of text) */
+    uint32_t threads;     /* threads per CTA (multiple of 32, <= 512) */
+    uint32_t chains;      /* independent chains per thread: 1, 2 or 4 */
+    uint32_t ctas;        /* persistent grid size; 0 = one per SM */
+    uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains) */
 } ac_scan_config;
 
 /* ------------------------------------------------------------ automaton */

@@ -503,6 +503,7 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
         ac_scan_config cfg = rep->cfg;
         if (!cfg.threads) cfg.threads = 512;
         if (!cfg.chains) cfg.chains = 2;
+        if (!cfg.stage_bytes) cfg.stage_bytes = (rep->K >= 8) ? 32 : 16;
         auto init_plan = [&](Plan &P) {
             P.device = device;
             P.fmt = fmt;
@@ -559,7 +560,7 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
             init_plan(*P);
             // autotune row length x CTA shape on this batch
             const uint32_t L0 = default_row_bytes(total, warm, cfg, device);
-            const ac_scan_config shapes[3] = {{0, 512, 2, 0}, {0, 256, 4, 0}, {0, 512, 1, 0}};
+            const ac_scan_config shapes[4] = {{0, 512, 2, 0, 32}, {0, 512, 4, 0, 16}, {0, 512, 2, 0, 16}, {0, 256, 4, 0, 32}};
             const uint32_t Ls[3] = {std::max<uint32_t>(kStageBytes, (L0 / 2 + 31) / 32 * 32), L0, L0 * 2};
             float best = 1e30f;
             ac_scan_config best_cfg = cfg;

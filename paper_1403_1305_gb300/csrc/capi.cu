@@ -342,6 +342,8 @@ int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
         return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 512");
     if (cfg->chains && cfg->chains != 1 && cfg->chains != 2 && cfg->chains != 4)
         return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
+    if (cfg->stage_bytes && cfg->stage_bytes != 16 && cfg->stage_bytes != 32)
+        return set_error(AC_EINVAL, "ac_set_scan_config: stage bytes must be 16 or 32");
     a->cfg = *cfg;
     return AC_OK;
 }

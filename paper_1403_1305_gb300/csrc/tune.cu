@@ -27,11 +27,13 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
     ac_scan_config best{};
     float best_ms = 1e30f;
     int rc = (num && keys) ? AC_OK : set_error(AC_ENOMEM, "ac_tune: scratch");
-    const uint32_t threads[2] = {256, 512}, chains[3] = {1, 2, 4};
+    const uint32_t threads[2] = {256, 512}, chains[3] = {1, 2, 4}, stages[2] = {16, 32};
     for (int ti = 0; ti < 2 && rc == AC_OK; ++ti)
         for (int ci = 0; ci < 3 && rc == AC_OK; ++ci)
+            for (int si = 0; si < 2 && rc == AC_OK; ++si)
             for (int li = 0; li < 3 && rc == AC_OK; ++li) {
-                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0};
+                if (stages[si] == 16 && chains[ci] == 1) continue;
+                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0, stages[si]};
                 ac_scan_config c;
                 default_config(a, n, fmt, &c);
                 c.row_len = li == 0 ? std::max<uint32_t>(64, c.row_len / 2) : li == 1 ? c.row_len : c.row_len * 2;

@@ -54,6 +54,8 @@ CONFIGS = [
     dict(row_len=48, threads=128, chains=4),
     dict(row_len=64, threads=256, chains=4, ctas=3),
     dict(row_len=0, threads=0, chains=0),
+    dict(row_len=32, threads=64, chains=2, stage_bytes=16),
+    dict(row_len=80, threads=128, chains=4, stage_bytes=16),
 ]
 
 
@@ -77,7 +79,7 @@ def test_hybrid_and_global_placement(smem):
     for i in range(60):
         text, pats = workloads.tiny_case(rng, b"ACGT", max_n=700, max_p=30, max_len=12, other_frac=0.02)
         a = A.ac_build(pats, alphabet="ACGT", placement=A.AC_PLACE_HYBRID, smem_table_bytes=smem)
-        A.ac_set_scan_config(a, row_len=32, threads=64, chains=2)
+        A.ac_set_scan_config(a, row_len=32, threads=64, chains=2, stage_bytes=16 if i % 2 else 32)
         same(A.ac_scan(a, text), oracle.scan(pats, text))
     a = A.ac_build(pats, alphabet="ACGT", placement=A.AC_PLACE_GLOBAL)
     same(A.ac_scan(a, text), oracle.scan(pats, text))
@@ -91,7 +93,7 @@ def test_packed_text_ragged_lengths():
         pats = workloads.draw_patterns(rng, [src, text] if n else src, 20, 1, 9, 0.5,
                                        np.frombuffer(b"ACGT", np.uint8))
         a = A.ac_build(pats, alphabet="ACGT")
-        A.ac_set_scan_config(a, row_len=128, threads=64, chains=2)
+        A.ac_set_scan_config(a, row_len=128, threads=64, chains=2, stage_bytes=16 if n % 2 else 32)
         want = oracle.scan(pats, text)
         packed = workloads.pack2(text)
         same(A.ac_scan(a, packed, n=n, fmt=A.AC_PACKED2), want)
