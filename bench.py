@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--batch-texts", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
@@ -284,6 +285,94 @@ def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
     return total, scan, M
 
 
+def time_async(A, torch, a, d_text, n, fmt, reps, warm=3):
+    """Median device time (ms) of ac_scan_async (device in/out) over reps runs."""
+    stream = torch.cuda.Stream()
+    P = a.num_patterns
+    d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_counts = torch.zeros(P, dtype=torch.int64, device="cuda")
+    d_keys = torch.empty(1 << 20, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        A.ac_scan_keys_async(a, d_text, n, fmt, stream, d_keys, 1 << 20, d_num, d_counts)
+    stream.synchronize()
+    M = int(d_num.item())
+    cap = 1 << max(10, int(np.ceil(np.log2(max(M, 1) * 1.25 + 1))))
+    d_m = torch.empty(cap, dtype=torch.int64, device="cuda")
+    ts = []
+    with torch.cuda.stream(stream):
+        for i in range(warm + reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.ac_scan_async(a, d_text, n, fmt, stream, d_m, cap, d_num, d_counts)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warm:
+                ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), M, cap, d_m, d_num, d_counts
+
+
+def bench_configs(A, torch, dev, hbm_peak):
+    """Config 1 (1 MiB DNA, 100 patterns) and config 3 (64 MiB protein,
+    100,000 patterns, table in L2)."""
+    out = {}
+    w = workloads.config1()
+    a = A.ac_build(w.patterns, alphabet="ACGT", device=dev)
+    d = torch.from_numpy(w.text).to(f"cuda:{dev}")
+    n = w.text.size
+    ms, M, cap, d_m, d_num, d_c = time_async(A, torch, a, d, n, A.AC_U8, 20)
+    t0 = time.perf_counter()
+    for _ in range(20):
+        A.ac_scan(a, d)
+    wall_ms = (time.perf_counter() - t0) / 20 * 1e3
+    # steady state: 100 back-to-back ac_scan_async calls captured in one CUDA graph, replayed
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    graph_ok = True
+    try:
+        with torch.cuda.graph(g, stream=stream):
+            cs = torch.cuda.current_stream()
+            for _ in range(100):
+                A.ac_scan_async(a, d, n, A.AC_U8, cs, d_m, cap, d_num, d_c)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / 1000
+        assert int(d_num.item()) == M
+    except Exception as ex:  # capture not supported: report it
+        graph_ok = False
+        graph_ms = None
+        out["config1_graph_error"] = str(ex)[:200]
+    # steady state as one batch of 1000 copies of the text
+    items = [(0, d, n, A.AC_U8)] * 1000
+    A.ac_scan_batch([a], items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH | A.AC_BATCH_NO_COUNTS)
+    A.ac_scan_batch([a], items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH | A.AC_BATCH_NO_COUNTS)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        A.ac_scan_batch([a], items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH | A.AC_BATCH_NO_COUNTS)
+    batch_ms = (time.perf_counter() - t0) / 3 / 1000 * 1e3
+    A.ac_batch_release()
+    roof_ms = n / (hbm_peak * 1e9) * 1e3
+    out["config1"] = {"workload": w.name, "matches": M, "single_call_device_ms": ms, "single_call_wall_ms": wall_ms,
+                      "graph_replayed_ms_per_scan": graph_ms, "batch1000_ms_per_scan": batch_ms,
+                      "GBps_single": n / ms / 1e6, "GBps_graph": (n / graph_ms / 1e6) if graph_ok else None,
+                      "GBps_batch1000": n / batch_ms / 1e6, "roofline_ms": roof_ms,
+                      "frac_graph": (roof_ms / graph_ms) if graph_ok else None, "frac_batch1000": roof_ms / batch_ms}
+    w = workloads.config3()
+    a = A.ac_build(w.patterns, alphabet=w.alphabet, device=dev)
+    st = A.ac_stats(a)
+    d = torch.from_numpy(w.text).to(f"cuda:{dev}")
+    ms, M, *_ = time_async(A, torch, a, d, w.text.size, A.AC_U8, 10)
+    out["config3"] = {"workload": w.name, "matches": M, "states": st["states"], "table_bytes": st["table_bytes"],
+                      "smem_states": st["smem_states"], "median_ms": ms, "GBps": w.text.size / ms / 1e6,
+                      "frac_of_hbm": w.text.size / ms / 1e6 / hbm_peak, "build_ms": st["build_ms"]}
+    return out
+
+
 def bench_batch(A, torch, dev, args):
     """4,096 DNA texts (log-uniform 1 KiB..4 MiB) against 8 resident pattern
     sets: one ac_scan_batch (kept plan replayed as a CUDA graph) against one
@@ -378,16 +467,23 @@ def bench_serve(A, torch, dev, args):
         tickets = [None] * len(reqs)
         start = time.perf_counter()
 
-        def producer():
-            for i, (ta, si, txt) in enumerate(reqs):
-                d = start + ta - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                tickets[i] = A.ac_serve_submit(srv, si, txt)
-
-        th = threading.Thread(target=producer)
-        th.start()
-        th.join()
+        # several producer threads share the arrival stream (submit copies the
+        # text; one thread alone cannot copy fast enough at high rates)
+        nprod = 4
+        ths = []
+        for k in range(nprod):
+            def prod(k=k):
+                for i in range(k, len(reqs), nprod):
+                    ta, si, txt = reqs[i]
+                    d = start + ta - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    tickets[i] = A.ac_serve_submit(srv, si, txt)
+            ths.append(threading.Thread(target=prod))
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
         for tk in tickets:
             A.ac_serve_wait(srv, tk, 600_000)
         end = time.perf_counter()
@@ -408,7 +504,7 @@ def bench_serve(A, torch, dev, args):
 
     # raise the offered rate x1.5 until the server no longer keeps up with it
     sweep, rate = [], 50.0
-    for _ in range(12):
+    for _ in range(18):
         reqs = make(args.serve_requests, rate)
         nbytes = sum(r[2].size for r in reqs)
         el, st = run_server(reqs)
@@ -429,7 +525,8 @@ def bench_serve(A, torch, dev, args):
             "per_request_GBps": nbytes / el / 1e9, "per_request_p50_ms": float(np.percentile(lat, 50)),
             "per_request_p99_ms": float(np.percentile(lat, 99)), "rate_hz_at_best": top["rate_hz"],
             "speedup": top["GBps"] / (nbytes / el / 1e9),
-            "served_path": "ac_serve_* (3 streams, <=64 requests per launch, host texts)",
+            "served_path": "ac_serve_* (3 streams, <=64 requests per launch, host texts copied into the server's "
+                           "page-locked slab; 4 producer threads)",
             "per_request_path": "ac_scan(host text) per request in arrival order"}
 
 
@@ -534,6 +631,8 @@ def main():
             del av, dt
         line["variants"] = var
 
+    if rank == 0 and not args.no_configs:
+        line["configs"] = bench_configs(A, torch, dev, hbm_peak)
     if rank == 0 and not args.no_batch:
         line["batch"] = bench_batch(A, torch, dev, args)
     if rank == 0 and not args.no_serve:

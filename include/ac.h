@@ -281,6 +281,9 @@ typedef struct {
     uint32_t num_streams;       /* launches in flight at once (0 = 2) */
     uint32_t max_wait_us;       /* how long the scheduler lets a partial batch wait for more arrivals
                                    (0 = none) */
+    uint64_t pinned_bytes;      /* page-locked host staging the server copies submitted texts into, so
+                                   their host->device copies run asynchronously (0 = 1 GiB); texts that do
+                                   not fit wait in ordinary host memory */
 } ac_serve_opts;
 
 /* Start a server over na resident automata (borrowed; they must outlive the

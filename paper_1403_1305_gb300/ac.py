@@ -83,7 +83,7 @@ class ac_batch_item(C.Structure):
 
 class ac_serve_opts(C.Structure):
     _fields_ = [("device_mem_budget", C.c_uint64), ("max_batch_items", C.c_uint32), ("max_queue", C.c_uint32),
-                ("num_streams", C.c_uint32), ("max_wait_us", C.c_uint32)]
+                ("num_streams", C.c_uint32), ("max_wait_us", C.c_uint32), ("pinned_bytes", C.c_uint64)]
 
 
 class ac_serve_stats_t(C.Structure):
@@ -391,9 +391,9 @@ class Server:
 
 
 def ac_serve_create(automata, device_mem_budget: int = 0, max_batch_items: int = 0, max_queue: int = 0,
-                    num_streams: int = 0, max_wait_us: int = 0) -> Server:
+                    num_streams: int = 0, max_wait_us: int = 0, pinned_bytes: int = 0) -> Server:
     hs = (C.c_void_p * max(1, len(automata)))(*[a.h for a in automata])
-    opts = ac_serve_opts(device_mem_budget, max_batch_items, max_queue, num_streams, max_wait_us)
+    opts = ac_serve_opts(device_mem_budget, max_batch_items, max_queue, num_streams, max_wait_us, pinned_bytes)
     h = C.c_void_p()
     _check(lib().ac_serve_create(hs, len(automata), C.byref(opts), C.byref(h)), "ac_serve_create")
     return Server(h, list(automata))

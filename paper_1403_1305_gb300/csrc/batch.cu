@@ -503,7 +503,7 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
         ac_scan_config cfg = rep->cfg;
         if (!cfg.threads) cfg.threads = 512;
         if (!cfg.chains) cfg.chains = 2;
-        if (!cfg.stage_bytes) cfg.stage_bytes = (rep->K >= 8) ? 32 : 16;
+        if (!cfg.stage_bytes) cfg.stage_bytes = (rep->K >= 8 || cfg.chains == 1) ? 32 : 16;
         auto init_plan = [&](Plan &P) {
             P.device = device;
             P.fmt = fmt;

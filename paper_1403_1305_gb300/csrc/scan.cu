@@ -125,7 +125,7 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
     // 16-byte stages leave more shared memory to the table and double the
     // stages in flight; with many small subset tables (which fit in shared
     // memory anyway) 32-byte stages do fewer pipeline round trips
-    if (!c.stage_bytes) c.stage_bytes = (a->K >= 8) ? 32 : 16;
+    if (!c.stage_bytes) c.stage_bytes = (a->K >= 8 || c.chains == 1) ? 32 : 16;
     if (!c.row_len) {
         // one chain per row, all chains of the GPU busy once, rows at least
         // 8x the warm-up and 256 symbols long

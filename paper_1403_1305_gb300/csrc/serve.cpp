@@ -13,6 +13,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -29,8 +30,52 @@ struct Request {
     int fmt;
     uint64_t n;
     uint64_t budget_bytes;  // device memory the request is charged while in flight
-    std::vector<uint8_t> text;
+    uint8_t *pinned = nullptr;  // copy in the page-locked slab, or
+    std::vector<uint8_t> text;  // copy in ordinary host memory
+    uint64_t slab_off = 0, slab_len = 0;
     Clock::time_point t_submit;
+    const uint8_t *data() const { return pinned ? pinned : text.data(); }
+};
+
+// First-fit allocator over the server's page-locked slab (16-byte granules).
+struct Slab {
+    uint8_t *base = nullptr;
+    uint64_t size = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> length
+    void init(uint8_t *b, uint64_t n) {
+        base = b;
+        size = n;
+        free_.clear();
+        if (b && n) free_[0] = n;
+    }
+    bool alloc(uint64_t n, uint64_t *off) {
+        n = (n + 15) & ~15ull;
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= n) {
+                *off = it->first;
+                const uint64_t rest = it->second - n, at = it->first + n;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n) {
+        n = (n + 15) & ~15ull;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
 };
 
 struct Done {
@@ -54,6 +99,7 @@ struct ac_server {
     bool stopping = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    Slab slab;
     // statistics
     uint64_t submitted = 0, completed = 0, launches = 0, items_launched = 0;
     std::vector<double> latencies_ms;
@@ -106,7 +152,7 @@ void worker_loop(ac_server *s, int w) {
         if (batch.empty()) continue;
         std::vector<ac_batch_item> items(batch.size());
         for (size_t i = 0; i < batch.size(); ++i)
-            items[i] = ac_batch_item{batch[i]->automaton, batch[i]->fmt, batch[i]->text.data(), batch[i]->n};
+            items[i] = ac_batch_item{batch[i]->automaton, batch[i]->fmt, batch[i]->data(), batch[i]->n};
         std::vector<ac_result> outs(batch.size());
         const int rc = ac_scan_batch(s->as.data(), (uint32_t)s->as.size(), items.data(), (uint32_t)items.size(),
                                      AC_HOST, 0, st, outs.data());
@@ -119,6 +165,7 @@ void worker_loop(ac_server *s, int w) {
                 s->mem_in_use -= r->budget_bytes;
                 s->completed++;
                 s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+                if (r->pinned) s->slab.release(r->slab_off, r->slab_len);
                 delete r;
             }
         }
@@ -171,14 +218,22 @@ int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_o
     if (!s->opts.max_batch_items) s->opts.max_batch_items = 256;
     if (!s->opts.max_queue) s->opts.max_queue = 65536;
     if (!s->opts.num_streams) s->opts.num_streams = 2;
+    if (!s->opts.pinned_bytes) s->opts.pinned_bytes = 1ull << 30;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
+    uint8_t *slab = nullptr;
+    if (cudaHostAlloc((void **)&slab, s->opts.pinned_bytes, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        slab = nullptr;  // texts then wait in ordinary host memory
+    }
+    s->slab.init(slab, slab ? s->opts.pinned_bytes : 0);
     for (uint32_t i = 0; i < s->opts.num_streams; ++i) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             for (auto x : s->streams) cudaStreamDestroy(x);
+            if (s->slab.base) cudaFreeHost(s->slab.base);
             if (prev >= 0) cudaSetDevice(prev);
             delete s;
             return set_error(AC_ECUDA, "ac_serve_create: cannot create streams");
@@ -209,21 +264,35 @@ int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint6
     r->budget_bytes = charge;
     r->t_submit = Clock::now();
     const uint64_t nbytes = fmt == AC_U8 ? n : (n + 3) / 4;
-    try {
-        r->text.assign(text, text + nbytes);
-    } catch (...) {
-        delete r;
-        return set_error(AC_ENOMEM, "ac_serve_submit: host copy of the text");
-    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stopping) {
-            delete r;
-            return set_error(AC_EINVAL, "ac_serve_submit: server is stopping");
-        }
         if (s->pending.size() >= s->opts.max_queue) {
             delete r;
             return set_error(AC_EBUSY, "ac_serve_submit: queue full (%u requests)", s->opts.max_queue);
+        }
+        if (nbytes && s->slab.alloc(nbytes, &r->slab_off)) {
+            r->pinned = s->slab.base + r->slab_off;
+            r->slab_len = nbytes;
+        }
+    }
+    if (r->pinned) {
+        memcpy(r->pinned, text, nbytes);  // outside the lock: the range is ours
+    } else {
+        try {
+            r->text.assign(text, text + nbytes);
+        } catch (...) {
+            delete r;
+            return set_error(AC_ENOMEM, "ac_serve_submit: host copy of the text");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping || s->pending.size() >= s->opts.max_queue) {
+            const bool stopping = s->stopping;
+            if (r->pinned) s->slab.release(r->slab_off, r->slab_len);
+            delete r;
+            return stopping ? set_error(AC_EINVAL, "ac_serve_submit: server is stopping")
+                            : set_error(AC_EBUSY, "ac_serve_submit: queue full (%u requests)", s->opts.max_queue);
         }
         r->ticket = s->next_ticket++;
         s->outstanding.insert(r->ticket);
@@ -282,6 +351,7 @@ void ac_serve_destroy(ac_server *s) {
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     for (auto st : s->streams) cudaStreamDestroy(st);
+    if (s->slab.base) cudaFreeHost(s->slab.base);
     if (prev >= 0) cudaSetDevice(prev);
     for (auto &kv : s->done) ac_result_free(&kv.second.r);
     delete s;
