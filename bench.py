@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-pfac", action="store_true")
     ap.add_argument("--batch-texts", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
@@ -373,6 +374,26 @@ def bench_configs(A, torch, dev, hbm_peak):
     return out
 
 
+def bench_pfac(A, torch, dev):
+    """The paper's method (failure-less machine, one walk per start position)
+    against the failure-folded table, same texts: build (host) and scan."""
+    out = {}
+    for name, w in (("config1", workloads.config1()), ("config2", workloads.config2()),
+                    ("config3", workloads.config3())):
+        alph = "ACGT" if w.alphabet == workloads.DNA else w.alphabet
+        d = torch.from_numpy(w.text).to(f"cuda:{dev}")
+        row = {}
+        for kind, mk in (("dfa", A.AC_MACHINE_DFA), ("pfac", A.AC_MACHINE_PFAC)):
+            a = A.ac_build(w.patterns, alphabet=alph, device=dev, machine=mk)
+            st = A.ac_stats(a)
+            ms, M, *_ = time_async(A, torch, a, d, w.text.size, A.AC_U8, 10)
+            row[kind] = {"build_ms": st["build_ms"], "scan_ms": ms, "GBps": w.text.size / ms / 1e6, "matches": M,
+                         "states": st["states"]}
+        row["same_matches"] = row["dfa"]["matches"] == row["pfac"]["matches"]
+        out[name] = row
+    return out
+
+
 def bench_batch(A, torch, dev, args):
     """4,096 DNA texts (log-uniform 1 KiB..4 MiB) against 8 resident pattern
     sets: one ac_scan_batch (kept plan replayed as a CUDA graph) against one
@@ -633,6 +654,8 @@ def main():
 
     if rank == 0 and not args.no_configs:
         line["configs"] = bench_configs(A, torch, dev, hbm_peak)
+    if rank == 0 and not args.no_pfac:
+        line["pfac"] = bench_pfac(A, torch, dev)
     if rank == 0 and not args.no_batch:
         line["batch"] = bench_batch(A, torch, dev, args)
     if rank == 0 and not args.no_serve:

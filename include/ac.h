@@ -74,6 +74,12 @@ extern "C" {
 #define AC_PLACE_HYBRID 2 /* the first (breadth-first) states in shared memory, the rest read through L2 */
 #define AC_PLACE_GLOBAL 3 /* every lookup through L2 / HBM */
 
+#define AC_MACHINE_DFA 0  /* failure transitions folded into a dense next-state table (Section III, AC-opt):
+                             one lookup per text symbol */
+#define AC_MACHINE_PFAC 1 /* failure-less machine (Section II.B, the paper's Section IV method): goto function
+                             only, built without a failure function; the scan walks from every text
+                             position until a missing transition */
+
 /* ------------------------------------------------------------ types */
 typedef struct ac_automaton ac_automaton;
 typedef struct ac_server ac_server;
@@ -92,6 +98,7 @@ typedef struct {
     int32_t placement;     /* AC_PLACE_* */
     int32_t device;        /* CUDA device ordinal; -1 builds on the host only (inspection, no scans) */
     uint32_t smem_table_bytes; /* cap on table bytes held in shared memory per CTA; 0 = as much as fits */
+    int32_t machine;           /* AC_MACHINE_DFA (default) or AC_MACHINE_PFAC; the results are the same */
 } ac_build_opts;
 
 typedef struct {

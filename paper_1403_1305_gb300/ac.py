@@ -26,6 +26,7 @@ AC_U8, AC_PACKED2 = 0, 1
 AC_HOST, AC_DEVICE = 0, 1
 AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL = 0, 1, 2, 3
 AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
+AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
@@ -48,7 +49,7 @@ class ac_match(C.Structure):
 
 class ac_build_opts(C.Structure):
     _fields_ = [("alphabet", C.c_char_p), ("num_subsets", C.c_uint32), ("placement", C.c_int32),
-                ("device", C.c_int32), ("smem_table_bytes", C.c_uint32)]
+                ("device", C.c_int32), ("smem_table_bytes", C.c_uint32), ("machine", C.c_int32)]
 
 
 class ac_result(C.Structure):
@@ -234,14 +235,14 @@ class Automaton:
 
 
 def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_PLACE_AUTO,
-             device: int = 0, smem_table_bytes: int = 0) -> Automaton:
+             device: int = 0, smem_table_bytes: int = 0, machine: int = AC_MACHINE_DFA) -> Automaton:
     pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
     bufs = [C.create_string_buffer(p, len(p)) if p else None for p in pats]
     ptrs = (C.c_void_p * max(1, len(pats)))(*[C.cast(b, C.c_void_p) if b is not None else None for b in bufs])
     lens = (C.c_uint32 * max(1, len(pats)))(*[len(p) for p in pats])
     if isinstance(alphabet, str):
         alphabet = alphabet.encode()
-    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes)
+    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine)
     h = C.c_void_p()
     _check(lib().ac_build(ptrs, lens, len(pats), C.byref(opts), C.byref(h)), "ac_build")
     return Automaton(h, len(pats), device)

@@ -15,6 +15,7 @@ namespace acgb {
 
 constexpr uint32_t kFlag = 0x80000000u;  // table entry bit: next state has a non-empty output
 constexpr uint32_t kStateMask = 0x7fffffffu;
+constexpr uint32_t kMissing = 0x7fffffffu;  // failure-less table: no transition
 
 // ---------------------------------------------------------------- host machine
 struct HostSubset {
@@ -66,6 +67,7 @@ struct ac_automaton {
     uint8_t byte_of_sym[256];
     bool dna_acgt = false;      // alphabet is exactly "ACGT" in this order
     int32_t placement = AC_PLACE_AUTO;
+    int32_t machine = AC_MACHINE_DFA;
     int32_t device = -1;
     uint32_t smem_cap_bytes = 0;
     std::vector<acgb::HostSubset> subs;
@@ -110,6 +112,9 @@ int scan_smem_limit(int device);
 uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
+                cudaStream_t stream);
+// failure-less machine: one walk per start position (pfac.cu)
+int launch_pfac(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
                 cudaStream_t stream);
 
 // Several texts laid out in one arena of whole rows (ac_scan_batch, serving).

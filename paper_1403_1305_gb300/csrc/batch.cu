@@ -436,9 +436,12 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
     if (mem != AC_HOST && mem != AC_DEVICE) return set_error(AC_EINVAL, "ac_scan_batch: unknown memory kind");
     for (uint32_t i = 0; i < ni; ++i) memset(&outs[i], 0, sizeof(ac_result));
     const int device = as[0] ? as[0]->device : -1;
-    for (uint32_t k = 0; k < na; ++k)
+    for (uint32_t k = 0; k < na; ++k) {
         if (!as[k] || as[k]->device != device || device < 0)
             return set_error(AC_EINVAL, "ac_scan_batch: automata must be built on one device");
+        if (as[k]->machine != AC_MACHINE_DFA)
+            return set_error(AC_EINVAL, "ac_scan_batch: batches take failure-folded (DFA) machines");
+    }
     for (uint32_t i = 0; i < ni; ++i) {
         const ac_batch_item &it = items[i];
         if (it.automaton >= na) return set_error(AC_EINVAL, "ac_scan_batch: item %u names automaton %u", i,

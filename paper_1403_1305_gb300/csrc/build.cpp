@@ -26,6 +26,80 @@ namespace {
 
 constexpr uint32_t kNone = 0xffffffffu;
 
+// Failure-less machine (Section II.B; the paper's Section IV method): the
+// goto function only, states renumbered breadth-first, each final state with
+// its own patterns; missing transitions stay missing (kMissing).
+int build_subset_pfac(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, uint32_t hi,
+                      const uint8_t *sym, uint32_t sigma, HostSubset &S, std::string &why) {
+    S.id_lo = lo;
+    S.id_hi = hi;
+    std::vector<uint32_t> child(sigma, kNone);
+    std::vector<uint32_t> depth(1, 0);
+    std::vector<std::pair<uint32_t, uint32_t>> finals;
+    finals.reserve(hi - lo);
+    uint64_t ns = 1;
+    for (uint32_t j = lo; j < hi; ++j) {
+        uint32_t s = 0;
+        S.max_len = std::max(S.max_len, lens[j]);
+        for (uint32_t k = 0; k < lens[j]; ++k) {
+            const uint64_t idx = (uint64_t)s * sigma + sym[pats[j][k]];
+            uint32_t t = child[idx];
+            if (t == kNone) {
+                if (ns >= (uint64_t)kMissing) {
+                    why = "more than 2^31-2 states in one subset";
+                    return AC_ERANGE;
+                }
+                t = (uint32_t)ns++;
+                child[idx] = t;
+                child.resize(ns * sigma, kNone);
+                depth.push_back(depth[s] + 1);
+            }
+            s = t;
+        }
+        finals.emplace_back(s, j);
+    }
+    const uint32_t N = (uint32_t)ns;
+    // breadth-first order over the goto edges
+    std::vector<uint32_t> order;
+    order.reserve(N);
+    order.push_back(0);
+    for (size_t h = 0; h < order.size(); ++h) {
+        const uint64_t rr = (uint64_t)order[h] * sigma;
+        for (uint32_t c = 0; c < sigma; ++c)
+            if (child[rr + c] != kNone) order.push_back(child[rr + c]);
+    }
+    std::vector<uint32_t> rank(N);
+    for (uint32_t i = 0; i < N; ++i) rank[order[i]] = i;
+    // own patterns per state (ids ascending: inserted in id order)
+    std::vector<uint32_t> cnt(N + 1, 0);
+    for (auto &f : finals) cnt[rank[f.first] + 1]++;
+    S.out_off.assign(N + 1, 0);
+    for (uint32_t i = 0; i < N; ++i) S.out_off[i + 1] = S.out_off[i] + cnt[i + 1];
+    S.out_ids.assign(finals.size(), 0);
+    std::vector<uint32_t> fill(S.out_off.begin(), S.out_off.end() - 1);
+    for (auto &f : finals) S.out_ids[fill[rank[f.first]]++] = f.second;
+    S.states = N;
+    S.table.resize((size_t)N * sigma);
+    S.fail.assign(N, 0);  // not built: the failure-less machine has none
+    S.depth.resize(N);
+    for (uint32_t i = 0; i < N; ++i) {
+        const uint32_t s = order[i];
+        S.depth[i] = depth[s];
+        const uint64_t rr = (uint64_t)s * sigma;
+        uint32_t *dst = &S.table[(size_t)i * sigma];
+        for (uint32_t c = 0; c < sigma; ++c) {
+            const uint32_t t = child[rr + c];
+            if (t == kNone) {
+                dst[c] = kMissing;
+            } else {
+                const uint32_t nx = rank[t];
+                dst[c] = nx | ((S.out_off[nx + 1] > S.out_off[nx]) ? kFlag : 0u);
+            }
+        }
+    }
+    return AC_OK;
+}
+
 int build_subset(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, uint32_t hi,
                  const uint8_t *sym, uint32_t sigma, HostSubset &S, std::string &why) {
     S.id_lo = lo;
@@ -204,7 +278,9 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
             if (k >= K) break;
             uint32_t lo = (uint32_t)((uint64_t)k * P / K), hi = (uint32_t)((uint64_t)(k + 1) * P / K);
             try {
-                rc[k] = build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
+                rc[k] = a->machine == AC_MACHINE_PFAC
+                            ? build_subset_pfac(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k])
+                            : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
             } catch (const std::bad_alloc &) {
                 rc[k] = AC_ENOMEM;
                 why[k] = "host allocation failed";

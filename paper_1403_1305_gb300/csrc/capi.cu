@@ -243,6 +243,11 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
         return set_error(AC_ENOMEM, "ac_build: host allocation");
     }
     a->placement = opts ? opts->placement : AC_PLACE_AUTO;
+    a->machine = opts ? opts->machine : AC_MACHINE_DFA;
+    if (a->machine != AC_MACHINE_DFA && a->machine != AC_MACHINE_PFAC) {
+        delete a;
+        return set_error(AC_EINVAL, "ac_build: unknown machine kind %d", opts->machine);
+    }
     a->device = opts ? opts->device : 0;
     a->smem_cap_bytes = opts ? opts->smem_table_bytes : 0;
     if (a->placement < AC_PLACE_AUTO || a->placement > AC_PLACE_GLOBAL) {

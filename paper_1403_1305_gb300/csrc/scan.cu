@@ -225,6 +225,7 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
 
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg_in,
                 cudaStream_t stream) {
+    if (a->machine == AC_MACHINE_PFAC) return launch_pfac(a, t, o, cfg_in, stream);
     ac_scan_config cfg = cfg_in;
     if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)
         return set_error(AC_EINVAL, "scan: threads per CTA must be a multiple of 32 in [32, 512]");

@@ -212,3 +212,30 @@ def test_config3_full_size():
     st = A.ac_stats(a)
     assert st["smem_states"] < st["states"]
     same(A.ac_scan(a, torch.from_numpy(w.text).cuda()), want)
+
+
+def test_failure_less_machine_scan():
+    """The paper's own method on the GPU (AC_MACHINE_PFAC): same results."""
+    rng = np.random.default_rng(71)
+    for i in range(150):
+        alph = (b"ACGT", b"ab", b"ACDEFGHIKLMNPQRSTVWY")[i % 3]
+        text, pats = workloads.tiny_case(rng, alph, max_n=5000 if i % 10 == 0 else 300, max_p=12, max_len=24,
+                                         other_frac=0.05 if i % 4 == 0 else 0.0)
+        K = 1 + (i % 2) if len(pats) >= 2 else 1
+        a = A.ac_build(pats, num_subsets=K, machine=A.AC_MACHINE_PFAC,
+                       smem_table_bytes=64 if i % 5 == 0 else 0)
+        same(A.ac_scan(a, text), oracle.scan(pats, text))
+    w = workloads.config1()
+    a = A.ac_build(w.patterns, alphabet="ACGT", machine=A.AC_MACHINE_PFAC)
+    same(A.ac_scan(a, torch.from_numpy(w.text).cuda()), oracle.scan(w.patterns, w.text))
+    w = workloads.config2(n=16 << 20)
+    a = A.ac_build(w.patterns, alphabet="ACGT", machine=A.AC_MACHINE_PFAC)
+    same(A.ac_scan(a, torch.from_numpy(w.text).cuda()), oracle.Machine(w.patterns).scan_mt(w.text, THREADS))
+    with pytest.raises(A.AcError):
+        A.ac_scan(a, torch.from_numpy(workloads.pack2(w.text)).cuda(), n=w.text.size, fmt=A.AC_PACKED2)
+
+
+def test_failure_less_machine_config3():
+    w = workloads.config3()
+    a = A.ac_build(w.patterns, alphabet=w.alphabet, machine=A.AC_MACHINE_PFAC)
+    same(A.ac_scan(a, torch.from_numpy(w.text).cuda()), oracle.Machine(w.patterns).scan_mt(w.text, THREADS))

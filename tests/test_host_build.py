@@ -147,3 +147,40 @@ def test_explicit_alphabet_order_sets_symbol_codes():
     sym = A.ac_subset(a, 0)["symbol_of_byte"]
     assert [sym[ord(c)] for c in "ACGT"] == [0, 1, 2, 3]
     assert sym[ord("N")] == 4
+
+
+def pfac_walk(a, text):
+    """The failure-less walk of Section II.B from every start, on the library's host table."""
+    v = A.ac_subset(a, 0)
+    T, off, ids, sym, sg = v["table"], v["out_off"], v["out_ids"], v["symbol_of_byte"], v["sigma"]
+    tb = np.frombuffer(text, np.uint8) if isinstance(text, bytes) else np.asarray(text, np.uint8)
+    res = []
+    for st in range(tb.size):
+        s = 0
+        for k in range(st, tb.size):
+            c = sym[tb[k]]
+            if c >= sg:
+                break
+            e = int(T[s, c])
+            if e == 0x7FFFFFFF:
+                break
+            s = e & 0x7FFFFFFF
+            if e >> 31:
+                res += [(k, int(j)) for j in ids[off[s]:off[s + 1]]]
+    res.sort()
+    return np.asarray(res, np.uint32).reshape(-1, 2)
+
+
+def test_failure_less_machine_tables():
+    """AC_MACHINE_PFAC builds the goto function only; walking it from every
+    start position gives the oracle's result, and Fig. 6's state numbers hold
+    after breadth-first renumbering of the same trie."""
+    rng = np.random.default_rng(31)
+    for i in range(300):
+        text, pats = workloads.tiny_case(rng, b"ACGT" if i % 2 else b"ab", max_n=60, max_p=8, max_len=6,
+                                         other_frac=0.05)
+        a = A.ac_build(pats, device=-1, machine=A.AC_MACHINE_PFAC)
+        assert np.array_equal(pfac_walk(a, text), oracle.scan(pats, text)[0]), (i, pats)
+    a = A.ac_build([b"HE", b"HIS", b"SHE", b"HERS"], device=-1, machine=A.AC_MACHINE_PFAC)
+    assert pfac_walk(a, b"USHERS").tolist() == [[3, 0], [3, 2], [5, 3]]
+    assert A.ac_stats(a)["states"] == oracle.Machine([b"HE", b"HIS", b"SHE", b"HERS"], False).num_states
