@@ -615,9 +615,9 @@ def main():
                        "l2": "text (256 MiB) larger than L2 (129 MB): no flush between steps",
                        "scan_config": A.ac_get_scan_config(a)},
             "roofline": roofline, "clocks": clocks,
-            "gpu_launches": 4 * args.steps,
-            "gpu_launches_note": "own kernels per step: scan, error mark, key pad, key->record convert "
-                                 "(plus the CUB radix-sort kernels compiled into the library)"}
+            "gpu_launches": 3 * args.steps,
+            "gpu_launches_note": "own kernels per step: scan, error mark, one-CTA key sort + record conversion "
+                                 "(plus three memset nodes)"}
 
     if not args.no_e2e:
         # end to end through the C ABI: pinned host text in, host results out

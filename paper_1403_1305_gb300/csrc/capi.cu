@@ -423,7 +423,17 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         }
         if (!keys) return set_error(AC_ERANGE, "ac_scan: output beyond capacity after a retry");
         const uint64_t M = h_num[0];
-        if (M) {
+        if (M && M <= kSmallSortMax) {
+            ac_match *d_m = (ac_match *)sc.get(M * sizeof(ac_match));
+            if (!d_m) return set_error(AC_ENOMEM, "ac_scan: records");
+            const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
+            e = launch_small_sort(keys, num, M, end_bit, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
+            if (e) return e;
+            r.matches = (ac_match *)malloc(M * sizeof(ac_match));
+            if (!r.matches) return set_error(AC_ENOMEM, "ac_scan: host matches");
+            CK(cudaMemcpyAsync(r.matches, d_m, M * sizeof(ac_match), cudaMemcpyDeviceToHost, s),
+               "ac_scan: copy matches");
+        } else if (M) {
             unsigned long long *alt = (unsigned long long *)sc.get(M * 8);
             if (!alt) return set_error(AC_ENOMEM, "ac_scan: sort buffer");
             const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
@@ -498,6 +508,11 @@ int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, cons
     DeviceGuard g(a->device);
     if (!g.ok) return set_error(AC_ECUDA, "ac_sort_keys_async: cannot use device %d", a->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (cap <= kSmallSortMax) {
+        const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n ? n - 1 : 0));
+        return launch_small_sort((const unsigned long long *)d_keys, (const unsigned long long *)d_num, cap, end_bit,
+                                 (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, nullptr, s);
+    }
     Scratch sc(s);
     const uint64_t kcap = cap ? cap : 1;
     unsigned long long *alt = (unsigned long long *)sc.get(kcap * 8);

@@ -2,6 +2,7 @@
 // memory), the small helper kernels (key padding, record conversion, error
 // mark), and the radix sort of the match keys. The scan kernel itself is in
 // scan_kernel.cuh (instantiated by the scan_k_*.cu translation units).
+#include <cub/block/block_radix_sort.cuh>
 #include <cub/device/device_radix_sort.cuh>
 
 #include "scan_kernel.cuh"
@@ -341,6 +342,60 @@ int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t
     mark_error_kernel<<<1, 1, 0, stream>>>(num, err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "mark: %s", cudaGetErrorString(e));
+}
+
+// Up to kSmallSortMax keys: one CTA loads the first min(M, cap) keys (the
+// rest as all-ones), radix-sorts them in shared memory and writes the
+// (position, id) records -- pad, sort and conversion in one launch.
+namespace {
+constexpr int kSmallThreads = 1024, kSmallItems = 8;
+using SmallSort = cub::BlockRadixSort<unsigned long long, kSmallThreads, kSmallItems>;
+
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    small_sort_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num, uint64_t cap,
+                      int end_bit, uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out,
+                      const uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char tmp[];
+    typename SmallSort::TempStorage &ts = *reinterpret_cast<typename SmallSort::TempStorage *>(tmp);
+    const unsigned long long M = *num;
+    const uint64_t m = M < cap ? M : cap;
+    unsigned long long k[kSmallItems];
+#pragma unroll
+    for (int i = 0; i < kSmallItems; ++i) {
+        const uint64_t idx = (uint64_t)threadIdx.x * kSmallItems + i;
+        k[i] = idx < m ? keys[idx] : ~0ull;
+    }
+    SmallSort(ts).Sort(k, 0, end_bit);
+    const unsigned long long mask = (1ull << shift) - 1ull;
+#pragma unroll
+    for (int i = 0; i < kSmallItems; ++i) {
+        const uint64_t idx = (uint64_t)threadIdx.x * kSmallItems + i;
+        if (idx < m) {
+            ac_match r;
+            r.pos = (uint32_t)(k[i] >> shift);
+            r.pattern_id = (uint32_t)(k[i] & mask);
+            out[idx] = r;
+        }
+    }
+    if (threadIdx.x == 0 && num_out) *num_out = (err && *err) ? ~0ull : M;
+}
+}  // namespace
+
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int end_bit,
+                      uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
+                      cudaStream_t stream) {
+    if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
+                                              (unsigned long long)kSmallSortMax);
+    const int smem = (int)sizeof(typename SmallSort::TempStorage);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(small_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    if (attr != cudaSuccess) return set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(attr));
+    small_sort_kernel<<<1, kSmallThreads, smem, stream>>>(keys, num, cap, end_bit, shift, out, num_out, err);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(e));
 }
 
 int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int end_bit, void *temp,

@@ -239,3 +239,27 @@ def test_failure_less_machine_config3():
     w = workloads.config3()
     a = A.ac_build(w.patterns, alphabet=w.alphabet, machine=A.AC_MACHINE_PFAC)
     same(A.ac_scan(a, torch.from_numpy(w.text).cuda()), oracle.Machine(w.patterns).scan_mt(w.text, THREADS))
+
+
+def test_async_sort_paths():
+    """Capacities at or below the one-CTA sort limit and above it (device radix sort)."""
+    import itertools
+    rng = np.random.default_rng(91)
+    pats = [bytes(p) for p in itertools.product(b"ACGT", repeat=4)]   # every window matches
+    a = A.ac_build(pats, alphabet="ACGT")
+    for n in (5000, 8195, 60_000):
+        text = workloads.dna_text(rng, n)
+        want = oracle.scan(pats, text)
+        M = want[0].shape[0]
+        dt = torch.from_numpy(text).cuda()
+        for cap in (M, M + 1, 8192, 1 << 17):
+            if cap < M:
+                continue
+            d_m = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
+            d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+            d_c = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+            A.ac_scan_async(a, dt, n, A.AC_U8, None, d_m, cap, d_num, d_c)
+            torch.cuda.synchronize()
+            assert int(d_num.item()) == M
+            got = d_m.view(-1, 2)[:M].cpu().numpy().view(np.uint32)
+            same((got, d_c.cpu().numpy().view(np.uint64)), want)
