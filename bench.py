@@ -221,8 +221,9 @@ def run_reference(args):
 # ---------------------------------------------------------------- our arm
 def kernel_source_hash():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1403_1305_gb300", "csrc", "scan.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("scan_kernel.cuh", "scan.cu"):
+        with open(os.path.join(ROOT, "paper_1403_1305_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
