@@ -150,6 +150,9 @@ typedef struct {
     uint32_t chains;      /* independent chains per thread: 1, 2 or 4 */
     uint32_t ctas;        /* persistent grid size; 0 = one per SM */
     uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains) */
+    uint32_t smem_table_bytes; /* cap on table bytes staged in shared memory for this scan (0 = the
+                                  automaton's cap or as much as fits); a smaller table leaves more of the
+                                  SM's memory to L1, which caches the rows a skewed text visits most */
 } ac_scan_config;
 
 /* ------------------------------------------------------------ automaton */

@@ -75,7 +75,7 @@ class ac_subset_view(C.Structure):
 
 class ac_scan_config(C.Structure):
     _fields_ = [("row_len", C.c_uint32), ("threads", C.c_uint32), ("chains", C.c_uint32), ("ctas", C.c_uint32),
-                ("stage_bytes", C.c_uint32)]
+                ("stage_bytes", C.c_uint32), ("smem_table_bytes", C.c_uint32)]
 
 
 class ac_batch_item(C.Structure):
@@ -276,8 +276,8 @@ def ac_subset(a: Automaton, k: int) -> dict:
 
 
 def ac_set_scan_config(a: Automaton, row_len: int = 0, threads: int = 0, chains: int = 0, ctas: int = 0,
-                       stage_bytes: int = 0):
-    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes)
+                       stage_bytes: int = 0, smem_table_bytes: int = 0):
+    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes, smem_table_bytes)
     _check(lib().ac_set_scan_config(a.h, C.byref(cfg)), "ac_set_scan_config")
 
 

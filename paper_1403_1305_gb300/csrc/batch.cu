@@ -563,13 +563,16 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
             init_plan(*P);
             // autotune row length x CTA shape on this batch
             const uint32_t L0 = default_row_bytes(total, warm, cfg, device);
-            const ac_scan_config shapes[4] = {{0, 512, 2, 0, 32}, {0, 512, 4, 0, 16}, {0, 512, 2, 0, 16}, {0, 256, 4, 0, 32}};
+            const ac_scan_config shapes[6] = {{0, 512, 2, 0, 32, 0}, {0, 512, 4, 0, 16, 0}, {0, 512, 2, 0, 16, 0},
+                                              {0, 256, 4, 0, 32, 0}, {0, 512, 2, 0, 16, 48u << 10},
+                                              {0, 512, 2, 0, 16, 16u << 10}};
             const uint32_t Ls[3] = {std::max<uint32_t>(kStageBytes, (L0 / 2 + 31) / 32 * 32), L0, L0 * 2};
             float best = 1e30f;
             ac_scan_config best_cfg = cfg;
             uint32_t best_L = L0;
             for (const auto &sh : shapes)
                 for (uint32_t L : Ls) {
+                    if (sh.smem_table_bytes && L != L0) continue;  // table size tried at the default row length
                     Plan T;
                     init_plan(T);
                     if (layout(as, items, idx, L, sh, flags | AC_BATCH_NO_COUNTS, T) != AC_OK) continue;

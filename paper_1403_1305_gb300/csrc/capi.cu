@@ -304,8 +304,9 @@ int ac_stats(const ac_automaton *a, ac_stats_t *o) {
         ac_scan_config c{};
         default_config(a, 1, AC_U8, &c);
         int limit = scan_smem_limit(a->device);
-        uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
+        uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 128);
         if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
+        if (c.smem_table_bytes && c.smem_table_bytes < avail) avail = c.smem_table_bytes;
         rows_fit = a->placement == AC_PLACE_GLOBAL ? 0 : (uint32_t)(avail / (4ull * a->sigma));
     }
     for (auto &s : a->subs) {

@@ -127,6 +127,14 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
     // stages in flight; with many small subset tables (which fit in shared
     // memory anyway) 32-byte stages do fewer pipeline round trips
     if (!c.stage_bytes) c.stage_bytes = (a->K >= 8 || c.chains == 1) ? 32 : 16;
+    if (!c.smem_table_bytes && a->sigma >= 16) {
+        // a large-alphabet table that does not fit: keep a small prefix in shared
+        // memory and leave the rest of the SRAM to L1, which follows the text's
+        // letter skew better than a fixed breadth-first prefix
+        uint64_t biggest = 0;
+        for (auto &d : a->h_desc) biggest = std::max<uint64_t>(biggest, (uint64_t)d.states * a->sigma * 4);
+        if (biggest > (160u << 10)) c.smem_table_bytes = 16u << 10;
+    }
     if (!c.row_len) {
         // one chain per row, all chains of the GPU busy once, rows at least
         // 8x the warm-up and 256 symbols long
@@ -152,6 +160,7 @@ int plan_smem(int device, const ac_scan_config &cfg, uint32_t sigma, int placeme
     if ((int)staging + 1024 > limit) return set_error(AC_EINVAL, "scan: staging does not fit in shared memory");
     uint64_t avail = (uint64_t)limit - staging - 128;
     if (smem_cap && smem_cap < avail) avail = smem_cap;
+    if (cfg.smem_table_bytes && cfg.smem_table_bytes < avail) avail = cfg.smem_table_bytes;
     uint32_t rows_fit = (uint32_t)(avail / (4ull * sigma));
     if (placement == AC_PLACE_GLOBAL) rows_fit = 0;
     *hybrid = max_states > rows_fit;

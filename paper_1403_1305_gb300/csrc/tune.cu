@@ -24,40 +24,71 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const ac_scan_config saved = a->cfg;
+    int rc = (num && keys) ? AC_OK : set_error(AC_ENOMEM, "ac_tune: scratch");
+    // time one configuration (best of 3); 1e30 if it cannot run
+    auto timeit = [&](ac_scan_config c) -> float {
+        ScanText t{d_text, n, fmt, nbytes};
+        ScanOut o{keys, cap, num, nullptr, (uint32_t *)(num + 1)};
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaMemsetAsync(num, 0, 16, s);
+            cudaEventRecord(e0, s);
+            if (launch_scan(a, t, o, c, s) != AC_OK) {
+                cudaGetLastError();
+                break;
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = set_error(AC_ECUDA, "ac_tune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms = std::min(best_ms, ms);
+        }
+        return best_ms;
+    };
+    // 1. CTA shape (threads x chains x stage bytes) at the default row length and table
     ac_scan_config best{};
     float best_ms = 1e30f;
-    int rc = (num && keys) ? AC_OK : set_error(AC_ENOMEM, "ac_tune: scratch");
     const uint32_t threads[2] = {256, 512}, chains[3] = {1, 2, 4}, stages[2] = {16, 32};
     for (int ti = 0; ti < 2 && rc == AC_OK; ++ti)
         for (int ci = 0; ci < 3 && rc == AC_OK; ++ci)
-            for (int si = 0; si < 2 && rc == AC_OK; ++si)
-            for (int li = 0; li < 3 && rc == AC_OK; ++li) {
+            for (int si = 0; si < 2 && rc == AC_OK; ++si) {
                 if (stages[si] == 16 && chains[ci] == 1) continue;
-                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0, stages[si]};
+                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0, stages[si], 0};
                 ac_scan_config c;
                 default_config(a, n, fmt, &c);
-                c.row_len = li == 0 ? std::max<uint32_t>(64, c.row_len / 2) : li == 1 ? c.row_len : c.row_len * 2;
-                ScanText t{d_text, n, fmt, nbytes};
-                ScanOut o{keys, cap, num, nullptr, (uint32_t *)(num + 1)};
-                float ms_best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
-                    cudaMemsetAsync(num, 0, 16, s);
-                    cudaEventRecord(e0, s);
-                    if (launch_scan(a, t, o, c, s) != AC_OK) break;
-                    cudaEventRecord(e1, s);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        rc = set_error(AC_ECUDA, "ac_tune: %s", cudaGetErrorString(cudaGetLastError()));
-                        break;
-                    }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    ms_best = std::min(ms_best, ms);
-                }
-                if (ms_best < best_ms) {
-                    best_ms = ms_best;
+                const float ms = timeit(c);
+                if (ms < best_ms) {
+                    best_ms = ms;
                     best = c;
                 }
             }
+    // 2. shared-memory table size (the rest goes through L1/L2)
+    const uint32_t caps[5] = {0, 96u << 10, 48u << 10, 16u << 10, 4u << 10};
+    ac_scan_config base = best;
+    for (int ki = 0; ki < 5 && rc == AC_OK; ++ki) {
+        ac_scan_config c = base;
+        c.smem_table_bytes = caps[ki];
+        if (caps[ki] == base.smem_table_bytes) continue;
+        const float ms = timeit(c);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    // 3. row length
+    base = best;
+    for (int li = 0; li < 2 && rc == AC_OK; ++li) {
+        ac_scan_config c = base;
+        c.row_len = li == 0 ? std::max<uint32_t>(64, base.row_len / 2) : base.row_len * 2;
+        const float ms = timeit(c);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
     cudaGetLastError();  // a candidate that did not fit (shared memory) is skipped
     a->cfg = (rc == AC_OK && best_ms < 1e29f) ? best : saved;
     if (chosen) *chosen = a->cfg;

@@ -263,3 +263,20 @@ def test_async_sort_paths():
             assert int(d_num.item()) == M
             got = d_m.view(-1, 2)[:M].cpu().numpy().view(np.uint32)
             same((got, d_c.cpu().numpy().view(np.uint64)), want)
+
+
+def test_tune_and_table_caps():
+    """ac_tune picks a configuration by timing; every shared-memory table cap
+    (down to none) and the tuned configuration give the oracle's result."""
+    w = workloads.config3(n=8 << 20, P=20_000)
+    want = oracle.Machine(w.patterns).scan_mt(w.text, THREADS)
+    a = A.ac_build(w.patterns, alphabet=w.alphabet)
+    d = torch.from_numpy(w.text).cuda()
+    for cap in (0, 64 << 10, 16 << 10, 4 << 10, 64):
+        A.ac_set_scan_config(a, smem_table_bytes=cap)
+        same(A.ac_scan(a, d), want)
+    A.ac_set_scan_config(a)
+    chosen = A.ac_tune(a, d)
+    assert chosen["threads"] in (256, 512) and chosen["chains"] in (1, 2, 4)
+    assert A.ac_get_scan_config(a) == chosen
+    same(A.ac_scan(a, d), want)
