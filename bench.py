@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-pfac", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--no-embedded", action="store_true")
     ap.add_argument("--batch-texts", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
@@ -395,6 +397,60 @@ def bench_pfac(A, torch, dev):
     return out
 
 
+def bench_paper_shapes(A, torch, dev):
+    """The shapes of the paper's Figs. 7-8 (Section V): 70 KB and 100 KB
+    inputs against 0.5 M / 1 M / 1.5 M patterns of about 20 bytes (10 / 20 /
+    30 MB of patterns). Throughput per Eq. (1): input bytes / total time,
+    where the total is machine construction (host), table upload and the scan
+    with results on the host -- the paper's time includes building the
+    machine. Both machine kinds; synthetic DNA (the paper's data is not
+    available). The 7337 B/s of the paper (failure-less machine, 1 thread,
+    AMD Opteron, 70 KB, 10 MB of patterns) is context, not a target."""
+    rng = np.random.default_rng(1176)
+    out = {}
+    for P in (500_000, 1_000_000, 1_500_000):
+        pats = workloads.random_patterns(rng, P, 15, 25, workloads.DNA)
+        mb = sum(len(p) for p in pats) / 1e6
+        texts = {kb: workloads.embed(rng, workloads.dna_text(rng, kb * 1000), pats, 50) for kb in (70, 100)}
+        rows = {kb: {} for kb in texts}
+        for kind, mk in (("dfa", A.AC_MACHINE_DFA), ("pfac", A.AC_MACHINE_PFAC)):
+            t0 = time.perf_counter()
+            a = A.ac_build(pats, alphabet="ACGT", device=dev, machine=mk)
+            build_s = time.perf_counter() - t0
+            st = A.ac_stats(a)
+            for kb, text in texts.items():
+                A.ac_scan(a, text)  # first-call overheads out of the way
+                t1 = time.perf_counter()
+                m, c = A.ac_scan(a, text)
+                scan_s = time.perf_counter() - t1
+                rows[kb][kind] = {"eq1_Bps": text.size / (build_s + scan_s), "build_total_ms": build_s * 1e3,
+                                  "build_ms": st["build_ms"], "upload_ms": st["upload_ms"], "scan_ms": scan_s * 1e3,
+                                  "scan_only_GBps": text.size / scan_s / 1e9, "states": st["states"],
+                                  "matches": int(m.shape[0])}
+            del a
+        for kb in texts:
+            rows[kb]["same_matches"] = rows[kb]["dfa"]["matches"] == rows[kb]["pfac"]["matches"]
+            out[f"{P // 1000}k_patterns_{mb:.0f}MB_{kb}KB"] = rows[kb]
+    return out
+
+
+def bench_embedded(A, torch, dev):
+    """Section V: two texts of the same size, one with patterns embedded and
+    one without, should take about the same search time."""
+    w = workloads.config2(n=64 << 20)
+    a = A.ac_build(w.patterns, alphabet="ACGT", device=dev)
+    rng = np.random.default_rng(1177)
+    plain = w.text
+    rich = workloads.embed(rng, plain, w.patterns, 100_000)
+    res = {}
+    for name, t in (("plain", plain), ("embedded_100k", rich)):
+        d = torch.from_numpy(t).to(f"cuda:{dev}")
+        ms, M, *_ = time_async(A, torch, a, d, t.size, A.AC_U8, 10)
+        res[name] = {"median_ms": ms, "matches": M}
+    res["time_ratio"] = res["embedded_100k"]["median_ms"] / res["plain"]["median_ms"]
+    return res
+
+
 def bench_batch(A, torch, dev, args):
     """4,096 DNA texts (log-uniform 1 KiB..4 MiB) against 8 resident pattern
     sets: one ac_scan_batch (kept plan replayed as a CUDA graph) against one
@@ -657,6 +713,10 @@ def main():
         line["configs"] = bench_configs(A, torch, dev, hbm_peak)
     if rank == 0 and not args.no_pfac:
         line["pfac"] = bench_pfac(A, torch, dev)
+    if rank == 0 and not args.no_paper:
+        line["paper_shapes"] = bench_paper_shapes(A, torch, dev)
+    if rank == 0 and not args.no_embedded:
+        line["embedded_check"] = bench_embedded(A, torch, dev)
     if rank == 0 and not args.no_batch:
         line["batch"] = bench_batch(A, torch, dev, args)
     if rank == 0 and not args.no_serve:

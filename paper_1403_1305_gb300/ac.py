@@ -237,14 +237,22 @@ class Automaton:
 def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_PLACE_AUTO,
              device: int = 0, smem_table_bytes: int = 0, machine: int = AC_MACHINE_DFA) -> Automaton:
     pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
-    bufs = [C.create_string_buffer(p, len(p)) if p else None for p in pats]
-    ptrs = (C.c_void_p * max(1, len(pats)))(*[C.cast(b, C.c_void_p) if b is not None else None for b in bufs])
-    lens = (C.c_uint32 * max(1, len(pats)))(*[len(p) for p in pats])
+    # one contiguous buffer; pattern j starts at offs[j] (empty patterns get a NULL pointer)
+    blob = np.frombuffer(b"".join(pats) or b"\0", dtype=np.uint8)
+    lens_np = np.fromiter((len(p) for p in pats), dtype=np.uint32, count=len(pats))
+    offs = np.zeros(len(pats), dtype=np.uint64)
+    if len(pats) > 1:
+        np.cumsum(lens_np[:-1], out=offs[1:])
+    addr = (offs + np.uint64(blob.ctypes.data)).astype(np.uint64)
+    addr[lens_np == 0] = 0
+    ptrs = addr.ctypes.data_as(C.POINTER(C.c_void_p)) if len(pats) else (C.c_void_p * 1)()
+    lens = lens_np.ctypes.data_as(C.POINTER(C.c_uint32)) if len(pats) else (C.c_uint32 * 1)()
     if isinstance(alphabet, str):
         alphabet = alphabet.encode()
     opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine)
     h = C.c_void_p()
     _check(lib().ac_build(ptrs, lens, len(pats), C.byref(opts), C.byref(h)), "ac_build")
+    del blob, addr, lens_np  # the library copied what it needs
     return Automaton(h, len(pats), device)
 
 

@@ -137,6 +137,7 @@ struct BatchLaunch {
     uint32_t smem_cap_bytes;
     int device;
     ac_scan_config cfg;          // threads and chains (row length is row_bytes)
+    uint32_t track_flags;        // record flagged steps in the fast loop
 };
 int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t stream);
 // shared-memory plan of a launch: table rows held in shared memory and the dynamic size

@@ -304,6 +304,7 @@ BatchLaunch launch_of(const Plan &P) {
     b.smem_cap_bytes = P.smem_cap;
     b.device = P.device;
     b.cfg = P.cfg;
+    b.track_flags = 1;  // a batch's machines each hold a whole pattern set
     return b;
 }
 

@@ -33,8 +33,12 @@ int build_subset_pfac(const uint8_t *const *pats, const uint32_t *lens, uint32_t
                       const uint8_t *sym, uint32_t sigma, HostSubset &S, std::string &why) {
     S.id_lo = lo;
     S.id_hi = hi;
+    uint64_t chars = 0;
+    for (uint32_t j = lo; j < hi; ++j) chars += lens[j];
     std::vector<uint32_t> child(sigma, kNone);
+    child.reserve((chars + 1) * sigma);
     std::vector<uint32_t> depth(1, 0);
+    depth.reserve(chars + 1);
     std::vector<std::pair<uint32_t, uint32_t>> finals;
     finals.reserve(hi - lo);
     uint64_t ns = 1;
@@ -105,8 +109,12 @@ int build_subset(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, 
     S.id_lo = lo;
     S.id_hi = hi;
     // 1. goto function (trie) with consecutive state numbers
+    uint64_t chars = 0;
+    for (uint32_t j = lo; j < hi; ++j) chars += lens[j];
     std::vector<uint32_t> child(sigma, kNone);
+    child.reserve((chars + 1) * sigma);
     std::vector<uint32_t> depth(1, 0);
+    depth.reserve(chars + 1);
     std::vector<std::pair<uint32_t, uint32_t>> finals;  // (state, pattern id)
     finals.reserve(hi - lo);
     uint64_t ns = 1;
@@ -175,23 +183,36 @@ int build_subset(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, 
     for (uint32_t i = 0; i < N; ++i) own_off[i + 1] += own_off[i];
     S.out_off.assign(N + 1, 0);
     S.out_ids.clear();
+    S.out_ids.reserve(finals.size() * 2);
     for (uint32_t i = 0; i < N; ++i) {
-        uint32_t t = order[i];
-        const uint32_t *own_b = nullptr;
-        size_t n_own = own_off[t + 1] - own_off[t];
-        std::vector<uint32_t> own(n_own);
-        for (size_t q = 0; q < n_own; ++q) own[q] = finals[own_off[t] + q].second;
-        size_t start = S.out_ids.size();
+        const uint32_t t = order[i];
+        // own ids: finals[own_off[t] .. own_off[t+1]) (ascending); merged with
+        // the output of the failure state, which comes earlier in this order
+        const size_t ob = own_off[t], oe = own_off[t + 1];
+        size_t fb = 0, fe = 0;
         if (i > 0) {
-            uint32_t fr = rank[fail[t]];  // fail[t] comes earlier in breadth-first order
-            size_t fb = S.out_off[fr], fe = S.out_off[fr + 1];
-            S.out_ids.resize(start + n_own + (fe - fb));
-            std::merge(own.begin(), own.end(), S.out_ids.begin() + fb, S.out_ids.begin() + fe,
-                       S.out_ids.begin() + start);
-        } else {
-            S.out_ids.insert(S.out_ids.end(), own.begin(), own.end());
+            const uint32_t fr = rank[fail[t]];
+            fb = S.out_off[fr];
+            fe = S.out_off[fr + 1];
         }
-        (void)own_b;
+        const size_t start = S.out_ids.size();
+        S.out_ids.resize(start + (oe - ob) + (fe - fb));
+        size_t a = ob, b = fb, w = start;
+        while (a < oe && b < fe) {
+            const uint32_t x = finals[a].second, y = S.out_ids[b];
+            if (x <= y) {
+                S.out_ids[w++] = x;
+                ++a;
+            } else {
+                S.out_ids[w++] = y;
+                ++b;
+            }
+        }
+        while (a < oe) S.out_ids[w++] = finals[a++].second;
+        while (b < fe) {
+            const uint32_t y = S.out_ids[b++];
+            S.out_ids[w++] = y;
+        }
         if (S.out_ids.size() > 0xffffffffull) {
             why = "output function larger than 2^32 entries";
             return AC_ERANGE;

@@ -47,10 +47,10 @@ __global__ void mark_error_kernel(unsigned long long *num, const uint32_t *err) 
 }
 
 // ------------------------------------------------------------------ dispatch
-KernelFn pick_kernel(int fmt, bool acgt, bool hybrid, uint32_t bx, uint32_t C, bool batch) {
-    if (fmt == AC_PACKED2) return kernels_packed(batch, hybrid, bx, C);
-    if (acgt) return kernels_u8_acgt(batch, hybrid, bx, C);
-    return kernels_u8_map(batch, hybrid, bx, C);
+KernelFn pick_kernel(int fmt, bool acgt, bool hybrid, uint32_t bx, uint32_t C, bool batch, bool track) {
+    if (fmt == AC_PACKED2) return kernels_packed(batch, track, hybrid, bx, C);
+    if (acgt) return kernels_u8_acgt(batch, track, hybrid, bx, C);
+    return kernels_u8_map(batch, track, hybrid, bx, C);
 }
 
 uint32_t bits_for(uint64_t x) {  // bits needed to hold values 0..x
@@ -220,7 +220,7 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
                    &p.table_words);
     if (rc) return rc;
     p.smem_rows = rows_used;
-    KernelFn fn = pick_kernel(b.fmt, b.fmt == AC_U8 && b.acgt, hybrid, bx, cfg.chains, true);
+    KernelFn fn = pick_kernel(b.fmt, b.fmt == AC_U8 && b.acgt, hybrid, bx, cfg.chains, true, b.track_flags != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "batch: %s", cudaGetErrorString(e));
     int sms = 148;
@@ -305,7 +305,9 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     p.smem_rows = rows_used;
 
     const bool acgt = t.fmt == AC_U8 && a->dna_acgt;
-    KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, bx, cfg.chains, false);
+    // one machine holding the whole pattern set: matches are frequent enough
+    // for flag tracking to pay; many subset machines: keep the loop lean
+    KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, bx, cfg.chains, false, a->K < 4);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
     int sms = 148;

@@ -1,0 +1,10 @@
+// Instantiations of the scan kernel: u8 acgt text, single launches, flag tracking off.
+#include "scan_kernel.cuh"
+
+namespace acgb {
+namespace kern {
+KernelFn kernels_u8_acgt_single_plain(bool hybrid, uint32_t bx, uint32_t C) {
+    return pick_variant<FMT_U8, ALPHA_ACGT, false, false>(hybrid, bx, C);
+}
+}  // namespace kern
+}  // namespace acgb

@@ -187,6 +187,14 @@ __device__ __forceinline__ uint32_t acgt_mismatch4(uint32_t w, uint32_t codes) {
     return expect ^ w;                                 // 0 iff all four bytes are ACGT
 }
 
+// count a flagged entry (next state with output) and remember the last one
+__device__ __forceinline__ void track_flag(uint32_t v, uint32_t step, uint32_t &cnt, uint32_t &fv, uint32_t &fi) {
+    const bool f = (int32_t)v < 0;
+    cnt += f ? 1u : 0u;
+    fv = f ? v : fv;
+    fi = f ? step : fi;
+}
+
 // ------------------------------------------------------------------ table lookups
 template <int MODE>
 __device__ __forceinline__ uint32_t lookup(const uint32_t *__restrict__ stab, const uint32_t *__restrict__ gtab,
@@ -252,25 +260,28 @@ __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool 
                                              const uint4 w0, const uint4 w1, const ChainText &ct,
                                              const ScanParams &p, const SubsetDev &sd, const uint32_t *stab,
                                              const uint8_t *smap, uint32_t hot, uint32_t lane) {
-    constexpr uint32_t SYM = (FMT == FMT_U8) ? BX : BX * 4;
     const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;  // symbols per 32-bit word
     uint32_t sc = s_in;
-    for (uint32_t i = 0; i < SYM; ++i) {
-        const int64_t pos = pos0 + i;
-        const bool live = active && pos >= 0 && pos < (int64_t)ct.nsym;
-        bool has = false;
-        if (live) {
-            const uint32_t bi = (FMT == FMT_U8) ? i : (i >> 2);
-            const uint32_t byte = (w[bi >> 2] >> (8 * (bi & 3))) & 0xffu;
-            const uint32_t c = (FMT == FMT_U8) ? (uint32_t)smap[byte] : (byte >> (2 * (i & 3))) & 3u;
-            uint32_t nv = 0;
-            if (c < p.sigma) nv = lookup<MODE_HYBRID>(stab, sd.table, hot, p.sigma, sc, c, l2_evict_last());
-            sc = nv & kStateMask;
-            has = main_stage && (nv & kFlag);
-        } else if (pos < 0) {
-            sc = 0;
+    // the word index is static (unrolled), so the stage stays in registers
+#pragma unroll
+    for (int e = 0; e < BX / 4; ++e) {
+        const uint32_t wv = w[e];
+        for (int b = 0; b < PER; ++b) {
+            const int64_t pos = pos0 + e * PER + b;
+            const bool live = active && pos >= 0 && pos < (int64_t)ct.nsym;
+            bool has = false;
+            if (live) {
+                const uint32_t c = (FMT == FMT_U8) ? (uint32_t)smap[(wv >> (8 * b)) & 0xffu] : (wv >> (2 * b)) & 3u;
+                uint32_t nv = 0;
+                if (c < p.sigma) nv = lookup<MODE_HYBRID>(stab, sd.table, hot, p.sigma, sc, c, l2_evict_last());
+                sc = nv & kStateMask;
+                has = main_stage && (nv & kFlag);
+            } else if (pos < 0) {
+                sc = 0;
+            }
+            emit_warp(has, sc, ct.vbase + (uint64_t)(pos < 0 ? 0 : pos), ct.cbase, sd, p, lane);
         }
-        emit_warp(has, sc, ct.vbase + (uint64_t)(pos < 0 ? 0 : pos), ct.cbase, sd, p, lane);
     }
     return sc;
 }
@@ -308,7 +319,7 @@ __device__ __forceinline__ bool chain_text(uint64_t row, const ScanParams &p, Ch
     return true;
 }
 
-template <int FMT, int ALPHA, int MODE, int BX, int C, bool BATCH>
+template <int FMT, int ALPHA, int MODE, int BX, int C, bool BATCH, bool TRACK>
 __global__ void __launch_bounds__(512, 1)
     scan_kernel(const __grid_constant__ ScanParams p, const __grid_constant__ CUtensorMap rows_map,
                 const __grid_constant__ CUtensorMap tail_map) {
@@ -443,8 +454,15 @@ __global__ void __launch_bounds__(512, 1)
             int64_t pos0[C];
             bool fast[C], dead[C], before[C];
             uint32_t v[C], acc[C], bad[C], s_in[C];
+            // flagged steps of each chain in this stage: how many, and the last
+            // one (its entry and step), so a stage with one match emits it
+            // without walking the stage again
+            uint32_t fcnt[C], fv[C], fi[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
+                fcnt[j] = 0;
+                fv[j] = 0;
+                fi[j] = 0;
                 const int64_t b0 = (int64_t)ct[j].row_in_text * L + o;
                 pos0[j] = (FMT == FMT_U8) ? b0 : b0 * 4;
                 dead[j] = !active[j] || pos0[j] >= (int64_t)ct[j].nsym;
@@ -474,6 +492,7 @@ __global__ void __launch_bounds__(512, 1)
                         for (int j = 0; j < C; ++j) {
                             v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (cw[j] >> (8 * b)) & 3u, tpol);
                             acc[j] |= v[j];
+                            if constexpr (TRACK) track_flag(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
@@ -488,6 +507,7 @@ __global__ void __launch_bounds__(512, 1)
                             const uint32_t nv = lookup<MODE>(stab, sd.table, hot, sigma, v[j], c < sigma ? c : 0u, tpol);
                             v[j] = c < sigma ? nv : 0u;
                             acc[j] |= v[j];
+                            if constexpr (TRACK) track_flag(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
@@ -501,23 +521,34 @@ __global__ void __launch_bounds__(512, 1)
                             v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (word_of(data[j][e >> 2], e & 3) >> (2 * b)) & 3u,
                                           tpol);
                             acc[j] |= v[j];
+                            if constexpr (TRACK) track_flag(v[j], e * 16 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
             }
-            bool need[C];
+            // TRACK (template): the fast loop counted flagged steps, so a stage
+            // with a single match emits it directly (pays off when matches are
+            // frequent or the scan waits on L2 anyway); off, any flagged stage is
+            // walked again (cheaper when the scan is issue-bound)
+            bool need[C], single[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (fast[j]) st8[j] = v[j] & kStateMask;
                 else if (before[j]) st8[j] = 0;
-                need[j] = !dead[j] && !before[j] && (!fast[j] || bad[j] != 0 || (main_stage && (acc[j] & kFlag)));
+                const bool flagged = TRACK ? fcnt[j] > 1 : (acc[j] & kFlag) != 0;
+                need[j] = !dead[j] && !before[j] && (!fast[j] || bad[j] != 0 || (main_stage && flagged));
+                single[j] = TRACK && !need[j] && fast[j] && main_stage && fcnt[j] == 1;
             }
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (__any_sync(kFull, need[j])) {
+                    // walked again by all lanes, emitting every flagged step of every lane
                     const uint32_t sc = careful_walk<FMT, BX>(s_in[j], pos0[j], active[j], main_stage, data[j][0],
                                                           data[j][1], ct[j], p, sd, stab, smap, hot, lane);
                     if (!dead[j]) st8[j] = sc;
+                } else if (__any_sync(kFull, single[j])) {
+                    emit_warp(single[j], fv[j] & kStateMask, ct[j].vbase + (uint64_t)(pos0[j] + fi[j]), ct[j].cbase, sd,
+                              p, lane);
                 }
             }
         }
@@ -535,25 +566,37 @@ __global__ void __launch_bounds__(512, 1)
 // ------------------------------------------------------------------ instantiation
 using KernelFn = void (*)(ScanParams, CUtensorMap, CUtensorMap);
 
-template <int FMT, int ALPHA, int MODE, bool BATCH>
+template <int FMT, int ALPHA, int MODE, bool BATCH, bool TRACK>
 KernelFn pick_shape(uint32_t bx, uint32_t C) {
-    if (bx == 16) return C == 4 ? scan_kernel<FMT, ALPHA, MODE, 16, 4, BATCH> : scan_kernel<FMT, ALPHA, MODE, 16, 2, BATCH>;
+    if (bx == 16)
+        return C == 4 ? scan_kernel<FMT, ALPHA, MODE, 16, 4, BATCH, TRACK> : scan_kernel<FMT, ALPHA, MODE, 16, 2, BATCH, TRACK>;
     switch (C) {
-        case 1: return scan_kernel<FMT, ALPHA, MODE, 32, 1, BATCH>;
-        case 2: return scan_kernel<FMT, ALPHA, MODE, 32, 2, BATCH>;
-        default: return scan_kernel<FMT, ALPHA, MODE, 32, 4, BATCH>;
+        case 1: return scan_kernel<FMT, ALPHA, MODE, 32, 1, BATCH, TRACK>;
+        case 2: return scan_kernel<FMT, ALPHA, MODE, 32, 2, BATCH, TRACK>;
+        default: return scan_kernel<FMT, ALPHA, MODE, 32, 4, BATCH, TRACK>;
     }
 }
 
-template <int FMT, int ALPHA, bool BATCH>
+template <int FMT, int ALPHA, bool BATCH, bool TRACK>
 KernelFn pick_variant(bool hybrid, uint32_t bx, uint32_t C) {
-    return hybrid ? pick_shape<FMT, ALPHA, MODE_HYBRID, BATCH>(bx, C) : pick_shape<FMT, ALPHA, MODE_SMEM, BATCH>(bx, C);
+    return hybrid ? pick_shape<FMT, ALPHA, MODE_HYBRID, BATCH, TRACK>(bx, C)
+                  : pick_shape<FMT, ALPHA, MODE_SMEM, BATCH, TRACK>(bx, C);
 }
 
 // defined in the scan_k_*.cu translation units (compiled in parallel)
-KernelFn kernels_u8_acgt(bool batch, bool hybrid, uint32_t bx, uint32_t C);
-KernelFn kernels_u8_map(bool batch, bool hybrid, uint32_t bx, uint32_t C);
-KernelFn kernels_packed(bool batch, bool hybrid, uint32_t bx, uint32_t C);
+#define AC_KERNEL_SET(name)                                                              \
+    KernelFn kernels_##name##_single_plain(bool hybrid, uint32_t bx, uint32_t C);       \
+    KernelFn kernels_##name##_single_track(bool hybrid, uint32_t bx, uint32_t C);       \
+    KernelFn kernels_##name##_batch_plain(bool hybrid, uint32_t bx, uint32_t C);        \
+    KernelFn kernels_##name##_batch_track(bool hybrid, uint32_t bx, uint32_t C);        \
+    inline KernelFn kernels_##name(bool batch, bool track, bool hybrid, uint32_t bx, uint32_t C) { \
+        if (batch) return track ? kernels_##name##_batch_track(hybrid, bx, C) : kernels_##name##_batch_plain(hybrid, bx, C); \
+        return track ? kernels_##name##_single_track(hybrid, bx, C) : kernels_##name##_single_plain(hybrid, bx, C); \
+    }
+AC_KERNEL_SET(u8_acgt)
+AC_KERNEL_SET(u8_map)
+AC_KERNEL_SET(packed)
+#undef AC_KERNEL_SET
 
 }  // namespace kern
 }  // namespace acgb

@@ -103,6 +103,36 @@ def draw_patterns(rng, texts, P, lo, hi, frac_sub, letters, probs=None, exclude=
     return [out[i] for i in order]
 
 
+def random_patterns(rng, P, lo, hi, letters):
+    """Exactly P distinct i.i.d. uniform patterns with lengths uniform in
+    [lo, hi] (vectorised, for pattern sets of millions)."""
+    letters = np.asarray(np.frombuffer(letters, np.uint8) if isinstance(letters, bytes) else letters, np.uint8)
+    out, seen = [], set()
+    while len(out) < P:
+        k = P - len(out)
+        lens = rng.integers(lo, hi + 1, size=k)
+        mat = letters[rng.integers(0, len(letters), size=(k, hi), dtype=np.uint8)]
+        for row, L in zip(mat, lens):
+            b = row[:L].tobytes()
+            if b not in seen:
+                seen.add(b)
+                out.append(b)
+    return out
+
+
+def embed(rng, text, patterns, count):
+    """A copy of text with `count` patterns (drawn uniformly) written at
+    uniform offsets."""
+    t = np.array(text, dtype=np.uint8, copy=True)
+    idx = rng.integers(0, len(patterns), size=count)
+    for i in idx:
+        p = np.frombuffer(patterns[int(i)], np.uint8)
+        if p.size <= t.size:
+            o = int(rng.integers(0, t.size - p.size + 1))
+            t[o:o + p.size] = p
+    return t
+
+
 def pack2(text: np.ndarray, alphabet: bytes = DNA) -> np.ndarray:
     """Pack a text over a 4-letter alphabet into 2-bit codes, 4 per byte.
 
