@@ -73,6 +73,16 @@ extern "C" {
 #define AC_PLACE_SMEM 1   /* whole table in shared memory; AC_ERANGE at build if it does not fit */
 #define AC_PLACE_HYBRID 2 /* the first (breadth-first) states in shared memory, the rest read through L2 */
 #define AC_PLACE_GLOBAL 3 /* every lookup through L2 / HBM */
+#define AC_PLACE_OPT 4    /* a power-of-two breadth-first prefix in shared memory, read without a per-lookup
+                             placement check; a stage of text that reaches a state beyond it is walked again
+                             (exact either way). AC_PLACE_AUTO picks it for a one-symbol scan when the states
+                             beyond the prefix are rarely reached (estimated from the patterns' letter
+                             frequencies); batched scans use AC_PLACE_HYBRID instead. */
+#define AC_PLACE_HYBRID16 5 /* 4-letter alphabets: a breadth-first prefix of 16-bit entries (next state + output
+                               bit, for the rows whose next states fit 15 bits: about twice the rows of
+                               AC_PLACE_HYBRID) in shared memory, the rest read through L2. AC_PLACE_AUTO picks
+                               it for a one-symbol scan when it leaves fewer lookups to L2; batched scans use
+                               AC_PLACE_HYBRID instead. */
 
 #define AC_MACHINE_DFA 0  /* failure transitions folded into a dense next-state table (Section III, AC-opt):
                              one lookup per text symbol */
@@ -99,6 +109,12 @@ typedef struct {
     int32_t device;        /* CUDA device ordinal; -1 builds on the host only (inspection, no scans) */
     uint32_t smem_table_bytes; /* cap on table bytes held in shared memory per CTA; 0 = as much as fits */
     int32_t machine;           /* AC_MACHINE_DFA (default) or AC_MACHINE_PFAC; the results are the same */
+    uint32_t stride;           /* symbols per table lookup the DFA machine is built for: 0 = automatic (1 and
+                                  2 for a 4-letter alphabet, else 1), 1 = one-symbol table only, 2 = also the
+                                  two-symbol table (4-letter alphabets and the DFA machine only, else
+                                  AC_EINVAL). The two-symbol table composes two transitions of the one-symbol
+                                  table (16 columns per state, 4x its memory) so a scan does one dependent
+                                  lookup per two text symbols; results are the same. */
 } ac_build_opts;
 
 typedef struct {
@@ -116,13 +132,17 @@ typedef struct {
     uint64_t states;         /* sum over subsets */
     uint64_t table_bytes;    /* sum over subsets of the dense goto tables */
     uint64_t output_entries; /* sum over states of |output(state)| */
-    uint64_t smem_states;    /* sum over subsets of the states held in shared memory */
+    uint64_t smem_states;    /* sum over subsets of the table rows a scan of byte text holds in shared memory */
     double build_ms;         /* host time of trie + failure + fold + renumber (all subsets) */
     double upload_ms;        /* host->device copy of the tables */
     int32_t device;
     uint32_t row_len;        /* current scan configuration (symbols per chain) */
     uint32_t threads;
     uint32_t chains;
+    uint64_t table2_bytes;   /* sum over subsets of the two-symbol tables (0 if not built) */
+    int32_t scan_placement;  /* the table placement (AC_PLACE_SMEM, _HYBRID, _OPT or _HYBRID16) and symbols per */
+    uint32_t scan_stride;    /* lookup a scan of byte text would use with the current configuration; -1 and 0
+                                when not applicable (host-only automaton, failure-less machine) */
 } ac_stats_t;
 
 /* Read-only host view of one subset machine (valid until ac_free). States are
@@ -141,6 +161,15 @@ typedef struct {
     const uint32_t *out_off; /* states + 1 */
     const uint32_t *out_ids;
     const uint8_t *symbol_of_byte; /* 256 entries; sigma = outside the alphabet */
+    /* two-symbol table (NULL if not built): table2[s*16 + c1 + 4*c2] = the state after symbols c1 then c2
+       from s (bits 0..29), bit 31 set when that state's output is not empty, bit 30 set when the output of
+       the state after c1 alone is not empty */
+    const uint32_t *table2;
+    /* 16-bit prefix (4-letter alphabets; NULL otherwise): rows [0, rows16) are the longest breadth-first prefix
+       whose next states all fit 15 bits; table16[s*4 + c] = (next << 1) | 1 if the next state's output is
+       not empty */
+    const uint16_t *table16;
+    uint32_t rows16;
 } ac_subset_view;
 
 /* Scan configuration (ac_set_scan_config / ac_tune). Zero fields = defaults. */
@@ -153,6 +182,10 @@ typedef struct {
     uint32_t smem_table_bytes; /* cap on table bytes staged in shared memory for this scan (0 = the
                                   automaton's cap or as much as fits); a smaller table leaves more of the
                                   SM's memory to L1, which caches the rows a skewed text visits most */
+    uint32_t stride;      /* symbols per lookup: 0 = automatic (2 when the automaton has its two-symbol
+                             table and the text is ACGT bytes or packed, else 1), 1, or 2 (AC_EINVAL at scan
+                             time when the two-symbol table or a suitable format is missing). Batched scans
+                             use 1. */
 } ac_scan_config;
 
 /* ------------------------------------------------------------ automaton */

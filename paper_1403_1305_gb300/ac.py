@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libacgb300.so")
 AC_OK, AC_EINVAL, AC_ENOMEM, AC_ERANGE, AC_ECUDA, AC_ETIMEDOUT, AC_EAGAIN, AC_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 AC_U8, AC_PACKED2 = 0, 1
 AC_HOST, AC_DEVICE = 0, 1
-AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL = 0, 1, 2, 3
+AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL, AC_PLACE_OPT, AC_PLACE_HYBRID16 = 0, 1, 2, 3, 4, 5
 AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
 AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
 
@@ -49,7 +49,8 @@ class ac_match(C.Structure):
 
 class ac_build_opts(C.Structure):
     _fields_ = [("alphabet", C.c_char_p), ("num_subsets", C.c_uint32), ("placement", C.c_int32),
-                ("device", C.c_int32), ("smem_table_bytes", C.c_uint32), ("machine", C.c_int32)]
+                ("device", C.c_int32), ("smem_table_bytes", C.c_uint32), ("machine", C.c_int32),
+                ("stride", C.c_uint32)]
 
 
 class ac_result(C.Structure):
@@ -62,7 +63,8 @@ class ac_stats_t(C.Structure):
                 ("max_len", C.c_uint32), ("states", C.c_uint64), ("table_bytes", C.c_uint64),
                 ("output_entries", C.c_uint64), ("smem_states", C.c_uint64), ("build_ms", C.c_double),
                 ("upload_ms", C.c_double), ("device", C.c_int32), ("row_len", C.c_uint32),
-                ("threads", C.c_uint32), ("chains", C.c_uint32)]
+                ("threads", C.c_uint32), ("chains", C.c_uint32), ("table2_bytes", C.c_uint64),
+                ("scan_placement", C.c_int32), ("scan_stride", C.c_uint32)]
 
 
 class ac_subset_view(C.Structure):
@@ -70,12 +72,13 @@ class ac_subset_view(C.Structure):
                 ("states", C.c_uint32), ("smem_states", C.c_uint32), ("table", C.POINTER(C.c_uint32)),
                 ("fail", C.POINTER(C.c_uint32)), ("depth", C.POINTER(C.c_uint32)),
                 ("out_off", C.POINTER(C.c_uint32)), ("out_ids", C.POINTER(C.c_uint32)),
-                ("symbol_of_byte", C.POINTER(C.c_uint8))]
+                ("symbol_of_byte", C.POINTER(C.c_uint8)), ("table2", C.POINTER(C.c_uint32)),
+                ("table16", C.POINTER(C.c_uint16)), ("rows16", C.c_uint32)]
 
 
 class ac_scan_config(C.Structure):
     _fields_ = [("row_len", C.c_uint32), ("threads", C.c_uint32), ("chains", C.c_uint32), ("ctas", C.c_uint32),
-                ("stage_bytes", C.c_uint32), ("smem_table_bytes", C.c_uint32)]
+                ("stage_bytes", C.c_uint32), ("smem_table_bytes", C.c_uint32), ("stride", C.c_uint32)]
 
 
 class ac_batch_item(C.Structure):
@@ -235,7 +238,8 @@ class Automaton:
 
 
 def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_PLACE_AUTO,
-             device: int = 0, smem_table_bytes: int = 0, machine: int = AC_MACHINE_DFA) -> Automaton:
+             device: int = 0, smem_table_bytes: int = 0, machine: int = AC_MACHINE_DFA,
+             stride: int = 0) -> Automaton:
     pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
     # one contiguous buffer; pattern j starts at offs[j] (empty patterns get a NULL pointer)
     blob = np.frombuffer(b"".join(pats) or b"\0", dtype=np.uint8)
@@ -249,7 +253,7 @@ def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_
     lens = lens_np.ctypes.data_as(C.POINTER(C.c_uint32)) if len(pats) else (C.c_uint32 * 1)()
     if isinstance(alphabet, str):
         alphabet = alphabet.encode()
-    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine)
+    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine, stride)
     h = C.c_void_p()
     _check(lib().ac_build(ptrs, lens, len(pats), C.byref(opts), C.byref(h)), "ac_build")
     del blob, addr, lens_np  # the library copied what it needs
@@ -280,12 +284,14 @@ def ac_subset(a: Automaton, k: int) -> dict:
     return {"id_lo": v.id_lo, "id_hi": v.id_hi, "max_len": v.max_len, "sigma": sigma, "states": S,
             "table": arr(v.table, S * sigma).reshape(S, sigma), "fail": arr(v.fail, S), "depth": arr(v.depth, S),
             "out_off": out_off, "out_ids": arr(v.out_ids, int(out_off[-1])),
-            "symbol_of_byte": arr(v.symbol_of_byte, 256, np.uint8)}
+            "symbol_of_byte": arr(v.symbol_of_byte, 256, np.uint8),
+            "table2": arr(v.table2, S * 16).reshape(S, 16) if v.table2 else None,
+            "table16": arr(v.table16, v.rows16 * 4, np.uint16).reshape(-1, 4) if v.table16 else None}
 
 
 def ac_set_scan_config(a: Automaton, row_len: int = 0, threads: int = 0, chains: int = 0, ctas: int = 0,
-                       stage_bytes: int = 0, smem_table_bytes: int = 0):
-    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes, smem_table_bytes)
+                       stage_bytes: int = 0, smem_table_bytes: int = 0, stride: int = 0):
+    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes, smem_table_bytes, stride)
     _check(lib().ac_set_scan_config(a.h, C.byref(cfg)), "ac_set_scan_config")
 
 

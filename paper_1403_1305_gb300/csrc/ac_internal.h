@@ -16,6 +16,10 @@ namespace acgb {
 constexpr uint32_t kFlag = 0x80000000u;  // table entry bit: next state has a non-empty output
 constexpr uint32_t kStateMask = 0x7fffffffu;
 constexpr uint32_t kMissing = 0x7fffffffu;  // failure-less table: no transition
+// two-symbol table entries: bit 31 = output at the second symbol, bit 30 = at the first
+constexpr uint32_t kFlag1 = 0x40000000u;
+constexpr uint32_t kStateMask2 = 0x3fffffffu;
+constexpr uint32_t kMaxStates2 = 1u << 28;  // s*16 + column must fit 32 bits
 
 // ---------------------------------------------------------------- host machine
 struct HostSubset {
@@ -27,11 +31,23 @@ struct HostSubset {
     std::vector<uint32_t> depth;
     std::vector<uint32_t> out_off;  // states + 1
     std::vector<uint32_t> out_ids;  // global ids, ascending per state
+    std::vector<uint32_t> table2;   // sigma = 4 only: states * 16, two symbols per entry (or empty)
+    // tail_mass[k] = sum over states s >= 2^k of the probability that an
+    // i.i.d. text (letters drawn with the patterns' letter frequencies) ends
+    // with s's string: an upper bound on the share of lookups at states >= 2^k
+    double tail_mass[32] = {};
+    // 16-bit prefix (sigma = 4): rows [0, rows16) whose next states all fit
+    // 15 bits; entry = (next state << 1) | 1 when its output is not empty
+    std::vector<uint16_t> table16;
+    uint32_t rows16 = 0;
 };
 
 // Device descriptor of one subset machine (array in device memory, one per subset).
 struct SubsetDev {
     const uint32_t *table;    // states * sigma
+    const uint32_t *table2;   // states * 16 (two-symbol table) or null
+    const uint16_t *table16;  // rows16 * 4 (16-bit prefix) or null
+    uint32_t rows16;
     const uint32_t *out_off;  // states + 1
     const uint32_t *out_ids;
     uint32_t states;
@@ -56,7 +72,8 @@ struct BatchTileDev {
 };
 
 struct DeviceSubset {
-    uint32_t *table = nullptr, *out_off = nullptr, *out_ids = nullptr;
+    uint32_t *table = nullptr, *out_off = nullptr, *out_ids = nullptr, *table2 = nullptr;
+    uint16_t *table16 = nullptr;
 };
 
 }  // namespace acgb
@@ -68,6 +85,7 @@ struct ac_automaton {
     bool dna_acgt = false;      // alphabet is exactly "ACGT" in this order
     int32_t placement = AC_PLACE_AUTO;
     int32_t machine = AC_MACHINE_DFA;
+    bool has_table2 = false;    // every subset has its two-symbol table
     int32_t device = -1;
     uint32_t smem_cap_bytes = 0;
     std::vector<acgb::HostSubset> subs;
@@ -85,6 +103,8 @@ namespace acgb {
 // build.cpp
 int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
                    ac_automaton *a);
+// symbols per lookup a scan of this format uses under configuration stride `want` (0 = automatic)
+uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want);
 
 // error reporting (capi.cu)
 int set_error(int code, const char *fmt, ...);
@@ -113,6 +133,18 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
                 cudaStream_t stream);
+// Table placement and symbols per lookup of a single-text scan (format fmt)
+// under configuration cfg (defaults filled in): kernel mode (the kernels'
+// MODE_* values), table rows staged in shared memory, words of shared memory
+// for the table, dynamic shared memory bytes.
+struct ScanPlan {
+    int mode = 0;
+    uint32_t stride = 1;
+    uint32_t smem_rows = 0;
+    uint32_t table_words = 0;
+    size_t smem = 0;
+};
+int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out);
 // failure-less machine: one walk per start position (pfac.cu)
 int launch_pfac(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
                 cudaStream_t stream);

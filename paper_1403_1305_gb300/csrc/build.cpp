@@ -240,6 +240,67 @@ int build_subset(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, 
     return AC_OK;
 }
 
+// Two-symbol table of a 4-letter machine: the composition of two transitions
+// of the folded table (a multi-symbol step of the AC-opt machine), so a scan
+// does one dependent lookup per two symbols. Column c1 + 4*c2 (the first
+// symbol in the low bits, as in packed text). Bit 31: the state after both
+// symbols has an output; bit 30: the state after c1 has one (the scan
+// recovers that state from the one-symbol table when it must emit).
+void build_table2(HostSubset &S) {
+    const uint32_t N = S.states;
+    S.table2.resize((size_t)N * 16);
+    for (uint32_t s = 0; s < N; ++s) {
+        const uint32_t *row = &S.table[(size_t)s * 4];
+        uint32_t *dst = &S.table2[(size_t)s * 16];
+        for (uint32_t c1 = 0; c1 < 4; ++c1) {
+            const uint32_t m = row[c1];
+            const uint32_t f1 = (m & kFlag) ? kFlag1 : 0u;
+            const uint32_t *mrow = &S.table[(size_t)(m & kStateMask) * 4];
+            for (uint32_t c2 = 0; c2 < 4; ++c2) {
+                const uint32_t e = mrow[c2];
+                dst[c1 + 4 * c2] = (e & kStateMask) | (e & kFlag) | f1;
+            }
+        }
+    }
+}
+
+// 16-bit prefix of a 4-letter machine: the longest breadth-first prefix of
+// rows whose next states all fit 15 bits, stored as (next << 1) | output
+// flag, so shared memory holds twice the rows of the 32-bit table.
+void build_table16(HostSubset &S) {
+    uint32_t rows = 0;
+    for (; rows < S.states; ++rows) {
+        const uint32_t *row = &S.table[(size_t)rows * 4];
+        if ((row[0] & kStateMask) > 0x7fffu || (row[1] & kStateMask) > 0x7fffu || (row[2] & kStateMask) > 0x7fffu ||
+            (row[3] & kStateMask) > 0x7fffu)
+            break;
+    }
+    S.rows16 = rows;
+    S.table16.resize((size_t)rows * 4);
+    for (size_t i = 0; i < S.table16.size(); ++i) {
+        const uint32_t e = S.table[i];
+        S.table16[i] = (uint16_t)(((e & 0x7fffu) << 1) | ((e & kFlag) ? 1u : 0u));
+    }
+}
+
+// Visit estimate for the placement choice: the probability of each state's
+// string under i.i.d. letters with probabilities prob[] (a goto child's is
+// its parent's times its letter's), summed over the states at or beyond each
+// power of two of the breadth-first order.
+void build_tail_mass(HostSubset &S, uint32_t sigma, const std::vector<double> &prob) {
+    const uint32_t N = S.states;
+    std::vector<double> p(N, 0.0);
+    p[0] = 1.0;
+    for (uint32_t s = 0; s < N; ++s)
+        for (uint32_t c = 0; c < sigma; ++c) {
+            const uint32_t t = S.table[(size_t)s * sigma + c] & kStateMask;
+            if (S.depth[t] == S.depth[s] + 1) p[t] = p[s] * prob[c];  // goto child
+        }
+    std::vector<double> suffix(N + 1, 0.0);
+    for (uint32_t s = N; s-- > 0;) suffix[s] = suffix[s + 1] + p[s];
+    for (int k = 0; k < 32; ++k) S.tail_mass[k] = (1ull << k) < N ? suffix[1ull << k] : 0.0;
+}
+
 }  // namespace
 
 int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
@@ -283,6 +344,21 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
     a->max_len = 0;
     for (uint32_t j = 0; j < P; ++j) a->max_len = std::max(a->max_len, lens[j]);
 
+    // two-symbol tables: asked for, or automatic for 4-letter DFA machines
+    const uint32_t stride = opts ? opts->stride : 0;
+    if (stride > 2) return set_error(AC_EINVAL, "ac_build: stride %u (0, 1 or 2)", stride);
+    if (stride == 2 && (sigma != 4 || a->machine != AC_MACHINE_DFA))
+        return set_error(AC_EINVAL, "ac_build: the two-symbol table needs a 4-letter alphabet and the DFA machine");
+    const bool want2 = a->machine == AC_MACHINE_DFA && sigma == 4 && stride != 1;
+
+    // letter frequencies of the patterns (add-one smoothed), for the visit estimate
+    std::vector<double> prob(sigma, 1.0);
+    double total = sigma;
+    for (uint32_t j = 0; j < P; ++j)
+        for (uint32_t k = 0; k < lens[j]; ++k) prob[a->sym_of_byte[pats[j][k]]] += 1.0;
+    for (uint32_t j = 0; j < P; ++j) total += lens[j];
+    for (auto &x : prob) x /= total;
+
     // subsets (a5)
     uint32_t K = (opts && opts->num_subsets) ? opts->num_subsets : 1;
     if (K > P) return set_error(AC_EINVAL, "ac_build: %u subsets for %u patterns", K, P);
@@ -302,6 +378,9 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
                 rc[k] = a->machine == AC_MACHINE_PFAC
                             ? build_subset_pfac(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k])
                             : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
+                if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA) build_tail_mass(a->subs[k], sigma, prob);
+                if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA && sigma == 4) build_table16(a->subs[k]);
+                if (rc[k] == AC_OK && want2 && a->subs[k].states < kMaxStates2) build_table2(a->subs[k]);
             } catch (const std::bad_alloc &) {
                 rc[k] = AC_ENOMEM;
                 why[k] = "host allocation failed";
@@ -317,6 +396,12 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
     }
     for (uint32_t k = 0; k < K; ++k)
         if (rc[k] != AC_OK) return set_error(rc[k], "ac_build: subset %u: %s", k, why[k].c_str());
+    a->has_table2 = want2;
+    for (auto &S : a->subs) a->has_table2 = a->has_table2 && !S.table2.empty();
+    if (stride == 2 && !a->has_table2)
+        return set_error(AC_ERANGE, "ac_build: two-symbol table needs fewer than 2^28 states per subset");
+    if (!a->has_table2)
+        for (auto &S : a->subs) std::vector<uint32_t>().swap(S.table2);
     a->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return AC_OK;
 }

@@ -125,6 +125,8 @@ static void free_device(ac_automaton *a) {
     DeviceGuard g(a->device);
     for (auto &d : a->dsubs) {
         cudaFree(d.table);
+        cudaFree(d.table2);
+        cudaFree(d.table16);
         cudaFree(d.out_off);
         cudaFree(d.out_ids);
     }
@@ -151,8 +153,19 @@ static int upload(ac_automaton *a) {
         if (!h.out_ids.empty())
             CK(cudaMemcpy(d.out_ids, h.out_ids.data(), h.out_ids.size() * 4, cudaMemcpyHostToDevice),
                "ac_build: copy");
+        if (!h.table2.empty()) {
+            CK(cudaMalloc(&d.table2, h.table2.size() * 4), "ac_build: two-symbol table");
+            CK(cudaMemcpy(d.table2, h.table2.data(), h.table2.size() * 4, cudaMemcpyHostToDevice), "ac_build: copy");
+        }
+        if (!h.table16.empty()) {
+            CK(cudaMalloc(&d.table16, h.table16.size() * 2), "ac_build: 16-bit prefix");
+            CK(cudaMemcpy(d.table16, h.table16.data(), h.table16.size() * 2, cudaMemcpyHostToDevice), "ac_build: copy");
+        }
         SubsetDev &s = a->h_desc[k];
         s.table = d.table;
+        s.table2 = d.table2;
+        s.table16 = d.table16;
+        s.rows16 = d.table16 ? h.rows16 : 0;
         s.out_off = d.out_off;
         s.out_ids = d.out_ids;
         s.states = h.states;
@@ -250,7 +263,7 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
     }
     a->device = opts ? opts->device : 0;
     a->smem_cap_bytes = opts ? opts->smem_table_bytes : 0;
-    if (a->placement < AC_PLACE_AUTO || a->placement > AC_PLACE_GLOBAL) {
+    if (a->placement < AC_PLACE_AUTO || a->placement > AC_PLACE_HYBRID16) {
         delete a;
         return set_error(AC_EINVAL, "ac_build: unknown placement %d", a->placement);
     }
@@ -299,21 +312,25 @@ int ac_stats(const ac_automaton *a, ac_stats_t *o) {
     o->num_subsets = a->K;
     o->sigma = a->sigma;
     o->max_len = a->max_len;
-    uint32_t rows_fit = 0;
-    if (a->device >= 0) {
+    // the plan a scan of byte text with the current configuration would use
+    ScanPlan plan{};
+    bool planned = false;
+    if (a->device >= 0 && a->machine == AC_MACHINE_DFA) {
         ac_scan_config c{};
         default_config(a, 1, AC_U8, &c);
-        int limit = scan_smem_limit(a->device);
-        uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 128);
-        if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
-        if (c.smem_table_bytes && c.smem_table_bytes < avail) avail = c.smem_table_bytes;
-        rows_fit = a->placement == AC_PLACE_GLOBAL ? 0 : (uint32_t)(avail / (4ull * a->sigma));
+        planned = plan_scan(a, c, AC_U8, &plan) == AC_OK;
     }
+    // kernel modes of the plan: 0 all rows, 1 hybrid, 2 optimistic prefix, 3 16-bit prefix
+    static const int32_t kPlacementOfMode[4] = {AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_OPT, AC_PLACE_HYBRID16};
+    o->scan_placement = planned ? kPlacementOfMode[plan.mode & 3] : -1;
+    o->scan_stride = planned ? plan.stride : 0;
     for (auto &s : a->subs) {
         o->states += s.states;
         o->table_bytes += (uint64_t)s.table.size() * 4;
         o->output_entries += s.out_ids.size();
-        o->smem_states += std::min<uint64_t>(s.states, rows_fit);
+        o->table2_bytes += (uint64_t)s.table2.size() * 4;
+        if (planned)
+            o->smem_states += std::min<uint64_t>(plan.mode == 3 ? s.rows16 : s.states, plan.smem_rows);
     }
     o->build_ms = a->build_ms;
     o->upload_ms = a->upload_ms;
@@ -339,6 +356,9 @@ int ac_subset(const ac_automaton *a, uint32_t k, ac_subset_view *v) {
     v->out_off = s.out_off.data();
     v->out_ids = s.out_ids.data();
     v->symbol_of_byte = a->sym_of_byte;
+    v->table2 = s.table2.empty() ? nullptr : s.table2.data();
+    v->table16 = s.table16.empty() ? nullptr : s.table16.data();
+    v->rows16 = s.rows16;
     return AC_OK;
 }
 
@@ -350,6 +370,9 @@ int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
         return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
     if (cfg->stage_bytes && cfg->stage_bytes != 16 && cfg->stage_bytes != 32)
         return set_error(AC_EINVAL, "ac_set_scan_config: stage bytes must be 16 or 32");
+    if (cfg->stride > 2) return set_error(AC_EINVAL, "ac_set_scan_config: stride must be 0, 1 or 2");
+    if (cfg->stride == 2 && !a->has_table2)
+        return set_error(AC_EINVAL, "ac_set_scan_config: stride 2 needs the automaton's two-symbol table");
     a->cfg = *cfg;
     return AC_OK;
 }

@@ -47,10 +47,28 @@ __global__ void mark_error_kernel(unsigned long long *num, const uint32_t *err) 
 }
 
 // ------------------------------------------------------------------ dispatch
-KernelFn pick_kernel(int fmt, bool acgt, bool hybrid, uint32_t bx, uint32_t C, bool batch, bool track) {
-    if (fmt == AC_PACKED2) return kernels_packed(batch, track, hybrid, bx, C);
-    if (acgt) return kernels_u8_acgt(batch, track, hybrid, bx, C);
-    return kernels_u8_map(batch, track, hybrid, bx, C);
+KernelFn pick_kernel(int fmt, bool acgt, int mode, uint32_t bx, uint32_t C, bool batch, bool track,
+                     uint32_t stride = 1) {
+    if (stride == 2) {  // single-text launches over ACGT bytes or packed text
+        if (fmt == AC_PACKED2)
+            return track ? kernels_packed_single_track_r2(mode, bx, C) : kernels_packed_single_plain_r2(mode, bx, C);
+        return track ? kernels_u8_acgt_single_track_r2(mode, bx, C) : kernels_u8_acgt_single_plain_r2(mode, bx, C);
+    }
+    if (fmt == AC_PACKED2) return kernels_packed(batch, track, mode, bx, C);
+    if (acgt) return kernels_u8_acgt(batch, track, mode, bx, C);
+    return kernels_u8_map(batch, track, mode, bx, C);
+}
+
+// Estimated share of lookups at states beyond a shared-memory prefix of
+// `rows` rows (the worst subset; tail masses are kept at powers of two, so
+// the prefix is rounded down to one).
+static double tail_beyond(const ac_automaton *a, uint32_t rows) {
+    if (rows == 0) return 1.0;
+    int k = 0;
+    while (k < 31 && (1u << (k + 1)) <= rows) ++k;
+    double worst = 0;
+    for (auto &S : a->subs) worst = std::max(worst, S.tail_mass[k]);
+    return worst;
 }
 
 uint32_t bits_for(uint64_t x) {  // bits needed to hold values 0..x
@@ -126,7 +144,7 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
     // 16-byte stages leave more shared memory to the table and double the
     // stages in flight; with many small subset tables (which fit in shared
     // memory anyway) 32-byte stages do fewer pipeline round trips
-    if (!c.stage_bytes) c.stage_bytes = (a->K >= 8 || c.chains == 1) ? 32 : 16;
+    if (!c.stage_bytes) c.stage_bytes = (a->K >= 4 || c.chains == 1) ? 32 : 16;
     if (!c.smem_table_bytes && a->sigma >= 16) {
         // a large-alphabet table that does not fit: keep a small prefix in shared
         // memory and leave the rest of the SRAM to L1, which follows the text's
@@ -134,6 +152,15 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
         uint64_t biggest = 0;
         for (auto &d : a->h_desc) biggest = std::max<uint64_t>(biggest, (uint64_t)d.states * a->sigma * 4);
         if (biggest > (160u << 10)) c.smem_table_bytes = 16u << 10;
+    }
+    if (!a->cfg.chains && a->device >= 0 && a->machine == AC_MACHINE_DFA) {
+        // with the 16-bit prefix (a large 4-letter machine) most steps still
+        // wait on L2 for some lane: 4 chains per thread keep more in flight
+        ScanPlan plan{};
+        if (plan_scan(a, c, fmt, &plan) == AC_OK && plan.mode == kern::MODE_H16) {
+            c.chains = 4;
+            if (!a->cfg.stage_bytes) c.stage_bytes = 16;
+        }
     }
     if (!c.row_len) {
         // one chain per row, all chains of the GPU busy once, rows at least
@@ -148,6 +175,94 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
         c.row_len = (uint32_t)L;
     }
     *cfg = c;
+}
+
+uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want) {
+    if (want == 1 || !a->has_table2) return 1;
+    const bool format_ok = fmt == AC_PACKED2 || (fmt == AC_U8 && a->dna_acgt);
+    if (want == 2) return format_ok ? 2 : 0;  // 0: asked for but not possible
+    return format_ok ? 2 : 1;
+}
+
+int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out) {
+    uint32_t max_states = 0, max_rows16 = 0;
+    bool has16 = a->sigma == 4 && !a->h_desc.empty();
+    for (auto &d : a->h_desc) {
+        max_states = std::max(max_states, d.states);
+        max_rows16 = std::max(max_rows16, d.rows16);
+        has16 = has16 && d.table16 && d.rows16 > 0;
+    }
+    uint32_t stride = scan_stride(a, fmt, cfg.stride);
+    if (stride == 0)
+        return set_error(AC_EINVAL, "scan: stride 2 needs the two-symbol table and ACGT bytes or packed text");
+    const uint32_t bx = cfg.stage_bytes ? cfg.stage_bytes : kStageBytes;
+    const uint32_t sym_per_stage = fmt == AC_U8 ? bx : 4 * bx;
+    ScanPlan one{}, two{};
+    bool hyb = false;
+    const int rc1 = plan_smem(a->device, cfg, a->sigma, a->placement, a->smem_cap_bytes, max_states, &one.smem_rows,
+                              &hyb, &one.smem, &one.table_words);
+    one.mode = hyb ? MODE_HYBRID : MODE_SMEM;
+    one.stride = 1;
+    if (stride == 2) {
+        bool hyb2 = false;
+        const int rc2 = plan_smem(a->device, cfg, 16, a->placement, a->smem_cap_bytes, max_states, &two.smem_rows,
+                                  &hyb2, &two.smem, &two.table_words);
+        two.mode = hyb2 ? MODE_HYBRID : MODE_SMEM;
+        two.stride = 2;
+        if (cfg.stride == 2) {
+            if (rc2) return rc2;
+            *out = two;
+            return AC_OK;
+        }
+        // automatic: two symbols per lookup pay when the one-symbol table
+        // overflows shared memory and the two-symbol prefix still holds
+        // nearly every state a walk visits
+        if (rc2 == AC_OK && rc1 == AC_OK && hyb && tail_beyond(a, two.smem_rows) <= 0.02) {
+            *out = two;
+            return AC_OK;
+        }
+    }
+    if (rc1) return rc1;
+    *out = one;
+    if (!hyb || one.smem_rows == 0 || (cfg.chains != 2 && cfg.chains != 4)) return AC_OK;
+    const int place = a->placement;
+    uint32_t rows_pow2 = 1;
+    while (rows_pow2 * 2 <= one.smem_rows) rows_pow2 *= 2;
+    if (place == AC_PLACE_OPT ||
+        (place == AC_PLACE_AUTO && tail_beyond(a, rows_pow2) * (32.0 * cfg.chains * sym_per_stage) < 0.01)) {
+        // MODE_OPT pays when a warp's stage rarely reaches a state beyond the
+        // power-of-two prefix (expected stages walked again below 1%)
+        out->mode = MODE_OPT;
+        out->smem_rows = rows_pow2;
+        out->table_words = (rows_pow2 * a->sigma + 3) & ~3u;
+        out->smem = (((size_t)out->table_words * 4 + 127) & ~(size_t)127) + scan_stage_bytes_per_cta(cfg);
+        return AC_OK;
+    }
+    if (has16 && (place == AC_PLACE_HYBRID16 || place == AC_PLACE_AUTO)) {
+        ScanPlan h{};
+        bool unused = false;
+        if (plan_smem(a->device, cfg, 2, AC_PLACE_AUTO, a->smem_cap_bytes, max_rows16, &h.smem_rows, &unused,
+                      &h.smem, &h.table_words) == AC_OK &&
+            h.smem_rows > 0) {
+            double m16 = 0;
+            for (auto &d : a->h_desc) {
+                const uint32_t staged = std::min(d.rows16, h.smem_rows);
+                int k = 0;
+                while (k < 31 && (1u << (k + 1)) <= staged) ++k;
+                const auto &S = a->subs[&d - a->h_desc.data()];
+                m16 = std::max(m16, staged ? S.tail_mass[k] : 1.0);
+            }
+            // the 16-bit lookup costs a little more per step: worth it when the
+            // 32-bit prefix leaves many lookups to L2 and the 16-bit one far fewer
+            const double m32 = tail_beyond(a, one.smem_rows);
+            if (place == AC_PLACE_HYBRID16 || (m32 >= 0.05 && m16 < 0.5 * m32)) {
+                h.mode = MODE_H16;
+                h.stride = 1;
+                *out = h;
+            }
+        }
+    }
+    return AC_OK;
 }
 
 int key_shift_for(const ac_automaton *a) { return (int)bits_for(a->P ? a->P - 1 : 0); }
@@ -220,7 +335,8 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
                    &p.table_words);
     if (rc) return rc;
     p.smem_rows = rows_used;
-    KernelFn fn = pick_kernel(b.fmt, b.fmt == AC_U8 && b.acgt, hybrid, bx, cfg.chains, true, b.track_flags != 0);
+    KernelFn fn = pick_kernel(b.fmt, b.fmt == AC_U8 && b.acgt, hybrid ? MODE_HYBRID : MODE_SMEM, bx, cfg.chains, true,
+                              b.track_flags != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "batch: %s", cudaGetErrorString(e));
     int sms = 148;
@@ -294,20 +410,20 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
         if (rc) return rc;
     }
 
-    uint32_t max_states = 0;
-    for (auto &d : a->h_desc) max_states = std::max(max_states, d.states);
-    uint32_t rows_used = 0;
-    bool hybrid = false;
-    size_t smem = 0;
-    rc = plan_smem(a->device, cfg, a->sigma, a->placement, a->smem_cap_bytes, max_states, &rows_used, &hybrid, &smem,
-                   &p.table_words);
+    ScanPlan plan{};
+    rc = plan_scan(a, cfg, t.fmt, &plan);
     if (rc) return rc;
-    p.smem_rows = rows_used;
+    p.smem_rows = plan.smem_rows;
+    p.table_words = plan.table_words;
+    const size_t smem = plan.smem;
+    const int mode = plan.mode;
+    const uint32_t stride = plan.stride;
 
     const bool acgt = t.fmt == AC_U8 && a->dna_acgt;
     // one machine holding the whole pattern set: matches are frequent enough
     // for flag tracking to pay; many subset machines: keep the loop lean
-    KernelFn fn = pick_kernel(t.fmt, acgt, hybrid, bx, cfg.chains, false, a->K < 4);
+    KernelFn fn = pick_kernel(t.fmt, acgt, mode, bx, cfg.chains, false, a->K < 4, stride);
+    if (!fn) return set_error(AC_EINVAL, "scan: no kernel for this configuration");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
     int sms = 148;

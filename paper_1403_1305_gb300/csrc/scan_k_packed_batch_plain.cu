@@ -3,8 +3,8 @@
 
 namespace acgb {
 namespace kern {
-KernelFn kernels_packed_batch_plain(bool hybrid, uint32_t bx, uint32_t C) {
-    return pick_variant<FMT_P2, ALPHA_MAP, true, false>(hybrid, bx, C);
+KernelFn kernels_packed_batch_plain(int mode, uint32_t bx, uint32_t C) {
+    return pick_variant<FMT_P2, ALPHA_MAP, true, false>(mode, bx, C);
 }
 }  // namespace kern
 }  // namespace acgb

@@ -3,8 +3,8 @@
 
 namespace acgb {
 namespace kern {
-KernelFn kernels_u8_acgt_batch_track(bool hybrid, uint32_t bx, uint32_t C) {
-    return pick_variant<FMT_U8, ALPHA_ACGT, true, true>(hybrid, bx, C);
+KernelFn kernels_u8_acgt_batch_track(int mode, uint32_t bx, uint32_t C) {
+    return pick_variant<FMT_U8, ALPHA_ACGT, true, true>(mode, bx, C);
 }
 }  // namespace kern
 }  // namespace acgb

@@ -3,8 +3,8 @@
 
 namespace acgb {
 namespace kern {
-KernelFn kernels_u8_acgt_single_plain(bool hybrid, uint32_t bx, uint32_t C) {
-    return pick_variant<FMT_U8, ALPHA_ACGT, false, false>(hybrid, bx, C);
+KernelFn kernels_u8_acgt_single_plain(int mode, uint32_t bx, uint32_t C) {
+    return pick_variant<FMT_U8, ALPHA_ACGT, false, false>(mode, bx, C);
 }
 }  // namespace kern
 }  // namespace acgb

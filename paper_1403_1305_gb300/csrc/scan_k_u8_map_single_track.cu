@@ -3,8 +3,8 @@
 
 namespace acgb {
 namespace kern {
-KernelFn kernels_u8_map_single_track(bool hybrid, uint32_t bx, uint32_t C) {
-    return pick_variant<FMT_U8, ALPHA_MAP, false, true>(hybrid, bx, C);
+KernelFn kernels_u8_map_single_track(int mode, uint32_t bx, uint32_t C) {
+    return pick_variant<FMT_U8, ALPHA_MAP, false, true>(mode, bx, C);
 }
 }  // namespace kern
 }  // namespace acgb

@@ -49,7 +49,11 @@ constexpr unsigned kFull = 0xffffffffu;
 
 enum { FMT_U8 = 0, FMT_P2 = 1 };
 enum { ALPHA_MAP = 0, ALPHA_ACGT = 1 };
-enum { MODE_SMEM = 0, MODE_HYBRID = 1 };
+// table placement of a launch: all rows in shared memory; a breadth-first
+// prefix in shared memory and the rest read through L2; a power-of-two
+// prefix read optimistically (see lookup); or, for 4-letter machines, a
+// prefix of 16-bit entries (ld_hybrid16) and the rest read through L2
+enum { MODE_SMEM = 0, MODE_HYBRID = 1, MODE_OPT = 2, MODE_H16 = 3 };
 
 // What a chain needs to know about the text its row belongs to.
 struct ChainText {
@@ -187,33 +191,89 @@ __device__ __forceinline__ uint32_t acgt_mismatch4(uint32_t w, uint32_t codes) {
     return expect ^ w;                                 // 0 iff all four bytes are ACGT
 }
 
-// count a flagged entry (next state with output) and remember the last one
+// count a flagged entry (an output at the step) and remember the last one
+template <uint32_t FLAGS>
 __device__ __forceinline__ void track_flag(uint32_t v, uint32_t step, uint32_t &cnt, uint32_t &fv, uint32_t &fi) {
-    const bool f = (int32_t)v < 0;
+    const bool f = (v & FLAGS) != 0;
     cnt += f ? 1u : 0u;
     fv = f ? v : fv;
     fi = f ? step : fi;
 }
 
 // ------------------------------------------------------------------ table lookups
+// Hybrid placement: one predicated pair, no branch. Lanes whose state lies in
+// the shared-memory prefix read it there, the others read the full table
+// through L2; a lane's word index is the same in both tables.
+__device__ __forceinline__ uint32_t ld_hybrid(const uint32_t *stab, const uint32_t *gtab, uint32_t s,
+                                              uint32_t smem_states, uint32_t idx, uint64_t pol) {
+    uint32_t v;
+    asm("{\n\t.reg .pred in_smem;\n\t.reg .u32 sa;\n\t.reg .u64 ga;\n\t"
+        "setp.lt.u32 in_smem, %1, %2;\n\t"
+        "mov.u32 %0, 0;\n\t"
+        "mad.lo.u32 sa, %3, 4, %4;\n\t"
+        "mad.wide.u32 ga, %3, 4, %5;\n\t"
+        "@in_smem ld.shared.u32 %0, [sa];\n\t"
+        "@!in_smem ld.global.nc.L2::cache_hint.u32 %0, [ga], %6;\n\t}"
+        : "=r"(v)
+        : "r"(s), "r"(smem_states), "r"(idx), "r"((uint32_t)__cvta_generic_to_shared(stab)), "l"(gtab), "l"(pol));
+    return v;
+}
+
+// Hybrid placement with a 16-bit prefix (sigma = 4): a shared-memory entry is
+// (next state << 1) | output bit; rotating it right by one bit gives the
+// 32-bit form next | kFlag. The two predicated loads write separate
+// registers (both start at zero, so an OR merges them).
+__device__ __forceinline__ uint32_t ld_hybrid16(const uint32_t *stab, const uint32_t *gtab, uint32_t s,
+                                                uint32_t smem_states, uint32_t idx, uint64_t pol) {
+    uint32_t h = 0, g = 0;
+    asm("{\n\t.reg .pred in_smem;\n\t.reg .u32 sa;\n\t.reg .u64 ga;\n\t"
+        "setp.lt.u32 in_smem, %2, %3;\n\t"
+        "mad.lo.u32 sa, %4, 2, %5;\n\t"
+        "mad.wide.u32 ga, %4, 4, %6;\n\t"
+        "@in_smem ld.shared.u16 %0, [sa];\n\t"
+        "@!in_smem ld.global.nc.L2::cache_hint.u32 %1, [ga], %7;\n\t}"
+        : "+r"(h), "+r"(g)
+        : "r"(s), "r"(smem_states), "r"(idx), "r"((uint32_t)__cvta_generic_to_shared(stab)), "l"(gtab), "l"(pol));
+    return g | __funnelshift_r(h, h, 1);
+}
+
+// MODE_OPT: the shared-memory prefix is a power of two of rows and the row
+// index is masked into it, so the read is always in bounds; a state beyond
+// the prefix reads a wrong entry, which the stage detects afterwards (the OR
+// of the stage's entries has a bit at or above the prefix's size) and
+// repairs by walking the stage again. smem_states is the prefix's row count.
 template <int MODE>
 __device__ __forceinline__ uint32_t lookup(const uint32_t *__restrict__ stab, const uint32_t *__restrict__ gtab,
                                            uint32_t smem_states, uint32_t sigma, uint32_t v, uint32_t c,
                                            uint64_t pol) {
-    uint32_t s = v & kStateMask;
+    const uint32_t s = v & kStateMask;
     if (MODE == MODE_SMEM) return stab[s * sigma + c];
-    if (s < smem_states) return stab[s * sigma + c];
-    return ld_table(gtab + (uint64_t)s * sigma + c, pol);
+    if (MODE == MODE_OPT) return stab[(s & (smem_states - 1)) * sigma + c];
+    if (MODE == MODE_H16) return ld_hybrid16(stab, gtab, s, smem_states, s * sigma + c, pol);
+    return ld_hybrid(stab, gtab, s, smem_states, s * sigma + c, pol);
 }
 
 template <int MODE>
 __device__ __forceinline__ uint32_t lookup4(const uint32_t *__restrict__ stab, const uint32_t *__restrict__ gtab,
                                             uint32_t smem_states, uint32_t v, uint32_t c, uint64_t pol) {
     // sigma = 4: index = s*4 + c; the shift drops the flag bit
-    uint32_t idx = (v << 2) | c;
+    const uint32_t idx = (v << 2) | c;
     if (MODE == MODE_SMEM) return stab[idx];
-    if ((v & kStateMask) < smem_states) return stab[idx];
-    return ld_table(gtab + (((uint64_t)(v & kStateMask)) << 2) + c, pol);
+    if (MODE == MODE_OPT) return stab[idx & (smem_states * 4u - 1u)];
+    if (MODE == MODE_H16) return ld_hybrid16(stab, gtab, v & kStateMask, smem_states, idx, pol);
+    return ld_hybrid(stab, gtab, v & kStateMask, smem_states, idx, pol);
+}
+
+// Two-symbol table (sigma = 4): index = s*16 + column, column = first symbol
+// + 4 * second symbol; bits 31 and 30 of the entry are flags, not state bits.
+template <int MODE>
+__device__ __forceinline__ uint32_t lookup16(const uint32_t *__restrict__ stab, const uint32_t *__restrict__ gtab2,
+                                             uint32_t smem_states, uint32_t v, uint32_t col, uint64_t pol) {
+    const uint32_t s = v & kStateMask2;
+    const uint32_t idx = (s << 4) | col;
+    if (MODE == MODE_SMEM) return stab[idx];
+    if (MODE == MODE_OPT) return stab[idx & (smem_states * 16u - 1u)];
+    return ld_hybrid(stab, gtab2, s, smem_states, idx, pol);
 }
 
 // Emit the output of state `sid` at position `pos` for every lane with
@@ -255,7 +315,7 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &w, int e) {
 // stage's BX bytes are in w0 (and w1 when BX = 32) (every byte of the text inside the stage is
 // there; positions before the text start reset the walk to the root). All 32
 // lanes call it together; returns the state after the stage.
-template <int FMT, int BX>
+template <int FMT, int BX, bool H16>
 __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool active, bool main_stage,
                                              const uint4 w0, const uint4 w1, const ChainText &ct,
                                              const ScanParams &p, const SubsetDev &sd, const uint32_t *stab,
@@ -274,13 +334,75 @@ __device__ __noinline__ uint32_t careful_walk(uint32_t s_in, int64_t pos0, bool 
             if (live) {
                 const uint32_t c = (FMT == FMT_U8) ? (uint32_t)smap[(wv >> (8 * b)) & 0xffu] : (wv >> (2 * b)) & 3u;
                 uint32_t nv = 0;
-                if (c < p.sigma) nv = lookup<MODE_HYBRID>(stab, sd.table, hot, p.sigma, sc, c, l2_evict_last());
+                if (c < p.sigma)
+                    nv = lookup<H16 ? MODE_H16 : MODE_HYBRID>(stab, sd.table, hot, p.sigma, sc, c, l2_evict_last());
                 sc = nv & kStateMask;
                 has = main_stage && (nv & kFlag);
             } else if (pos < 0) {
                 sc = 0;
             }
             emit_warp(has, sc, ct.vbase + (uint64_t)(pos < 0 ? 0 : pos), ct.cbase, sd, p, lane);
+        }
+    }
+    return sc;
+}
+
+// The careful walk of a two-symbol-table scan: pairs of symbols through the
+// two-symbol table (rows in shared memory as staged), the first symbol's
+// state read from the one-symbol table only where it has an output; pairs
+// at the text's end or holding a byte outside ACGT go symbol by symbol
+// through the one-symbol table. Stage starts are even positions, so a pair
+// never straddles the text start.
+template <int FMT, int BX>
+__device__ __noinline__ uint32_t careful_walk2(uint32_t s_in, int64_t pos0, bool active, bool main_stage,
+                                              const uint4 w0, const uint4 w1, const ChainText &ct,
+                                              const ScanParams &p, const SubsetDev &sd, const uint32_t *stab,
+                                              const uint8_t *smap, uint32_t hot, uint32_t lane) {
+    const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;  // symbols per 32-bit word
+    const uint64_t pol = l2_evict_last();
+    uint32_t sc = s_in;
+#pragma unroll
+    for (int e = 0; e < BX / 4; ++e) {
+        const uint32_t wv = w[e];
+        for (int h = 0; h < PER / 2; ++h) {
+            const int64_t pos = pos0 + e * PER + 2 * h;
+            uint32_t c1, c2;
+            if (FMT == FMT_U8) {
+                c1 = smap[(wv >> (16 * h)) & 0xffu];
+                c2 = smap[(wv >> (16 * h + 8)) & 0xffu];
+            } else {
+                c1 = (wv >> (4 * h)) & 3u;
+                c2 = (wv >> (4 * h + 2)) & 3u;
+            }
+            const bool live1 = active && pos >= 0 && pos < (int64_t)ct.nsym;
+            const bool live2 = active && pos + 1 >= 0 && pos + 1 < (int64_t)ct.nsym;
+            bool has1 = false, has2 = false;
+            uint32_t mid = 0;
+            if (live1 && live2 && c1 < 4u && c2 < 4u) {
+                const uint32_t nv = ld_hybrid(stab, sd.table2, sc, hot, (sc << 4) | c1 | (c2 << 2), pol);
+                has1 = main_stage && (nv & kFlag1);
+                has2 = main_stage && (nv & kFlag);
+                if (has1) mid = ld_table(sd.table + ((uint64_t)sc << 2) + c1, pol) & kStateMask;
+                sc = nv & kStateMask2;
+            } else {
+                if (live1) {
+                    const uint32_t nv = c1 < 4u ? ld_table(sd.table + ((uint64_t)sc << 2) + c1, pol) : 0u;
+                    mid = sc = nv & kStateMask;
+                    has1 = main_stage && (nv & kFlag);
+                } else if (pos < 0) {
+                    sc = 0;
+                }
+                if (live2) {
+                    const uint32_t nv = c2 < 4u ? ld_table(sd.table + ((uint64_t)sc << 2) + c2, pol) : 0u;
+                    sc = nv & kStateMask;
+                    has2 = main_stage && (nv & kFlag);
+                } else if (pos + 1 < 0) {
+                    sc = 0;
+                }
+            }
+            emit_warp(has1, mid, ct.vbase + (uint64_t)(pos < 0 ? 0 : pos), ct.cbase, sd, p, lane);
+            emit_warp(has2, sc, ct.vbase + (uint64_t)(pos + 1 < 0 ? 0 : pos + 1), ct.cbase, sd, p, lane);
         }
     }
     return sc;
@@ -319,7 +441,7 @@ __device__ __forceinline__ bool chain_text(uint64_t row, const ScanParams &p, Ch
     return true;
 }
 
-template <int FMT, int ALPHA, int MODE, int BX, int C, bool BATCH, bool TRACK>
+template <int FMT, int ALPHA, int MODE, int BX, int C, bool BATCH, bool TRACK, int R>
 __global__ void __launch_bounds__(512, 1)
     scan_kernel(const __grid_constant__ ScanParams p, const __grid_constant__ CUtensorMap rows_map,
                 const __grid_constant__ CUtensorMap tail_map) {
@@ -327,6 +449,10 @@ __global__ void __launch_bounds__(512, 1)
     constexpr uint32_t SYM_PER_STAGE = (FMT == FMT_U8) ? BX : BX * 4;
     constexpr uint32_t SLOT = slot_bytes_for(C, BX);
     constexpr uint32_t BOX = 32u * BX;  // bytes of one chain group's box
+    // R = symbols per lookup: 1 (one-symbol table) or 2 (two-symbol table, sigma = 4)
+    static_assert(R == 1 || (R == 2 && (FMT == FMT_P2 || ALPHA == ALPHA_ACGT)), "two-symbol table needs ACGT");
+    constexpr uint32_t FLAGS = R == 2 ? (kFlag | kFlag1) : kFlag;
+    constexpr uint32_t SMASK = R == 2 ? kStateMask2 : kStateMask;
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t *stab = reinterpret_cast<uint32_t *>(smem);
@@ -363,14 +489,22 @@ __global__ void __launch_bounds__(512, 1)
             tile_row0 = (tile / p.K) * p.rows_per_tile;
         }
         const SubsetDev sd = p.subs[k];
-        const uint32_t hot = min(sd.states, p.smem_rows);
+        // rows staged in shared memory
+        const uint32_t hot = min(MODE == MODE_H16 ? sd.rows16 : sd.states, p.smem_rows);
+        // fast-loop lookups: MODE_OPT masks with the launch's power-of-two row
+        // count (a smaller subset's states all lie below it, so its indices
+        // pass the mask unchanged)
+        const uint32_t lk = MODE == MODE_OPT ? p.smem_rows : hot;
         if ((int)k != cur_k) {
             __syncthreads();  // every warp is done with the previous table
-            const uint32_t words = hot * sigma;
-            const uint4 *src4 = reinterpret_cast<const uint4 *>(sd.table);
+            const uint32_t *src = MODE == MODE_H16 ? reinterpret_cast<const uint32_t *>(sd.table16)
+                                  : R == 2          ? sd.table2
+                                                    : sd.table;
+            const uint32_t words = MODE == MODE_H16 ? hot * 2u : hot * (R == 2 ? 16u : sigma);
+            const uint4 *src4 = reinterpret_cast<const uint4 *>(src);
             uint4 *dst4 = reinterpret_cast<uint4 *>(stab);
             for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) dst4[i] = __ldg(src4 + i);
-            for (uint32_t i = (words & ~3u) + threadIdx.x; i < words; i += blockDim.x) stab[i] = __ldg(sd.table + i);
+            for (uint32_t i = (words & ~3u) + threadIdx.x; i < words; i += blockDim.x) stab[i] = __ldg(src + i);
             __syncthreads();
             cur_k = (int)k;
         }
@@ -473,10 +607,49 @@ __global__ void __launch_bounds__(512, 1)
                 acc[j] = 0;
                 bad[j] = 0;
             }
-            // The C chains advance together, one symbol each per round, so their
+            // The C chains advance together, one lookup each per round, so their
             // lookups are independent and overlap. Chains off the fast path walk
             // in-bounds garbage that is discarded.
-            if (FMT == FMT_U8 && ALPHA == ALPHA_ACGT) {
+            if constexpr (R == 2) {
+                if constexpr (FMT == FMT_U8) {
+#pragma unroll
+                    for (int e = 0; e < (int)(BX / 4); ++e) {
+                        uint32_t cw[C];
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            const uint32_t w = word_of(data[j][e >> 2], e & 3);
+                            cw[j] = acgt_codes4(w);
+                            bad[j] |= acgt_mismatch4(w, cw[j]);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int j = 0; j < C; ++j) {
+                                // codes of bytes 2h and 2h+1 -> column c1 + 4*c2
+                                const uint32_t col = ((cw[j] >> (16 * h)) & 3u) | ((cw[j] >> (16 * h + 6)) & 12u);
+                                v[j] = lookup16<MODE>(stab, sd.table2, lk, v[j], col, tpol);
+                                acc[j] |= v[j];
+                                if constexpr (TRACK) track_flag<FLAGS>(v[j], e * 2 + h, fcnt[j], fv[j], fi[j]);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < (int)(BX / 4); ++e) {
+#pragma unroll
+                        for (int h = 0; h < 8; ++h) {
+#pragma unroll
+                            for (int j = 0; j < C; ++j) {
+                                // a nibble of packed text is the column (first symbol in its low bits)
+                                const uint32_t col = (word_of(data[j][e >> 2], e & 3) >> (4 * h)) & 15u;
+                                v[j] = lookup16<MODE>(stab, sd.table2, lk, v[j], col, tpol);
+                                acc[j] |= v[j];
+                                if constexpr (TRACK) track_flag<FLAGS>(v[j], e * 8 + h, fcnt[j], fv[j], fi[j]);
+                            }
+                        }
+                    }
+                }
+            } else if (FMT == FMT_U8 && ALPHA == ALPHA_ACGT) {
 #pragma unroll
                 for (int e = 0; e < (int)(BX / 4); ++e) {
                     uint32_t cw[C];
@@ -490,9 +663,9 @@ __global__ void __launch_bounds__(512, 1)
                     for (int b = 0; b < 4; ++b) {
 #pragma unroll
                         for (int j = 0; j < C; ++j) {
-                            v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (cw[j] >> (8 * b)) & 3u, tpol);
+                            v[j] = lookup4<MODE>(stab, sd.table, lk, v[j], (cw[j] >> (8 * b)) & 3u, tpol);
                             acc[j] |= v[j];
-                            if constexpr (TRACK) track_flag(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
+                            if constexpr (TRACK) track_flag<kFlag>(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
@@ -504,10 +677,10 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
                         for (int j = 0; j < C; ++j) {
                             const uint32_t c = smap[(word_of(data[j][e >> 2], e & 3) >> (8 * b)) & 0xffu];
-                            const uint32_t nv = lookup<MODE>(stab, sd.table, hot, sigma, v[j], c < sigma ? c : 0u, tpol);
+                            const uint32_t nv = lookup<MODE>(stab, sd.table, lk, sigma, v[j], c < sigma ? c : 0u, tpol);
                             v[j] = c < sigma ? nv : 0u;
                             acc[j] |= v[j];
-                            if constexpr (TRACK) track_flag(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
+                            if constexpr (TRACK) track_flag<kFlag>(v[j], e * 4 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
@@ -518,10 +691,10 @@ __global__ void __launch_bounds__(512, 1)
                     for (int b = 0; b < 16; ++b) {
 #pragma unroll
                         for (int j = 0; j < C; ++j) {
-                            v[j] = lookup4<MODE>(stab, sd.table, hot, v[j], (word_of(data[j][e >> 2], e & 3) >> (2 * b)) & 3u,
+                            v[j] = lookup4<MODE>(stab, sd.table, lk, v[j], (word_of(data[j][e >> 2], e & 3) >> (2 * b)) & 3u,
                                           tpol);
                             acc[j] |= v[j];
-                            if constexpr (TRACK) track_flag(v[j], e * 16 + b, fcnt[j], fv[j], fi[j]);
+                            if constexpr (TRACK) track_flag<kFlag>(v[j], e * 16 + b, fcnt[j], fv[j], fi[j]);
                         }
                     }
                 }
@@ -533,22 +706,32 @@ __global__ void __launch_bounds__(512, 1)
             bool need[C], single[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                if (fast[j]) st8[j] = v[j] & kStateMask;
+                if (fast[j]) st8[j] = v[j] & SMASK;
                 else if (before[j]) st8[j] = 0;
-                const bool flagged = TRACK ? fcnt[j] > 1 : (acc[j] & kFlag) != 0;
-                need[j] = !dead[j] && !before[j] && (!fast[j] || bad[j] != 0 || (main_stage && flagged));
+                // with the two-symbol table a single flagged step is emitted
+                // directly only when its output is at the second symbol
+                const bool flagged = TRACK ? (fcnt[j] > 1 || (R == 2 && fcnt[j] == 1 && (fv[j] & kFlag1)))
+                                           : (acc[j] & FLAGS) != 0;
+                // MODE_OPT: a state at or beyond the prefix was looked up
+                const bool outside = MODE == MODE_OPT && ((acc[j] | s_in[j]) & SMASK) >= lk;
+                need[j] = !dead[j] && !before[j] && (!fast[j] || bad[j] != 0 || outside || (main_stage && flagged));
                 single[j] = TRACK && !need[j] && fast[j] && main_stage && fcnt[j] == 1;
             }
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (__any_sync(kFull, need[j])) {
                     // walked again by all lanes, emitting every flagged step of every lane
-                    const uint32_t sc = careful_walk<FMT, BX>(s_in[j], pos0[j], active[j], main_stage, data[j][0],
-                                                          data[j][1], ct[j], p, sd, stab, smap, hot, lane);
+                    uint32_t sc;
+                    if constexpr (R == 2)
+                        sc = careful_walk2<FMT, BX>(s_in[j], pos0[j], active[j], main_stage, data[j][0], data[j][1],
+                                                    ct[j], p, sd, stab, smap, hot, lane);
+                    else
+                        sc = careful_walk<FMT, BX, MODE == MODE_H16>(s_in[j], pos0[j], active[j], main_stage, data[j][0], data[j][1],
+                                                   ct[j], p, sd, stab, smap, hot, lane);
                     if (!dead[j]) st8[j] = sc;
                 } else if (__any_sync(kFull, single[j])) {
-                    emit_warp(single[j], fv[j] & kStateMask, ct[j].vbase + (uint64_t)(pos0[j] + fi[j]), ct[j].cbase, sd,
-                              p, lane);
+                    emit_warp(single[j], fv[j] & SMASK, ct[j].vbase + (uint64_t)(pos0[j] + R * fi[j] + (R - 1)),
+                              ct[j].cbase, sd, p, lane);
                 }
             }
         }
@@ -566,37 +749,61 @@ __global__ void __launch_bounds__(512, 1)
 // ------------------------------------------------------------------ instantiation
 using KernelFn = void (*)(ScanParams, CUtensorMap, CUtensorMap);
 
-template <int FMT, int ALPHA, int MODE, bool BATCH, bool TRACK>
+template <int FMT, int ALPHA, int MODE, bool BATCH, bool TRACK, int R>
 KernelFn pick_shape(uint32_t bx, uint32_t C) {
     if (bx == 16)
-        return C == 4 ? scan_kernel<FMT, ALPHA, MODE, 16, 4, BATCH, TRACK> : scan_kernel<FMT, ALPHA, MODE, 16, 2, BATCH, TRACK>;
+        return C == 4 ? scan_kernel<FMT, ALPHA, MODE, 16, 4, BATCH, TRACK, R> : scan_kernel<FMT, ALPHA, MODE, 16, 2, BATCH, TRACK, R>;
     switch (C) {
-        case 1: return scan_kernel<FMT, ALPHA, MODE, 32, 1, BATCH, TRACK>;
-        case 2: return scan_kernel<FMT, ALPHA, MODE, 32, 2, BATCH, TRACK>;
-        default: return scan_kernel<FMT, ALPHA, MODE, 32, 4, BATCH, TRACK>;
+        case 1: return scan_kernel<FMT, ALPHA, MODE, 32, 1, BATCH, TRACK, R>;
+        case 2: return scan_kernel<FMT, ALPHA, MODE, 32, 2, BATCH, TRACK, R>;
+        default: return scan_kernel<FMT, ALPHA, MODE, 32, 4, BATCH, TRACK, R>;
     }
 }
 
-template <int FMT, int ALPHA, bool BATCH, bool TRACK>
-KernelFn pick_variant(bool hybrid, uint32_t bx, uint32_t C) {
-    return hybrid ? pick_shape<FMT, ALPHA, MODE_HYBRID, BATCH, TRACK>(bx, C)
-                  : pick_shape<FMT, ALPHA, MODE_SMEM, BATCH, TRACK>(bx, C);
+// mode: MODE_SMEM, MODE_HYBRID, MODE_OPT or MODE_H16 (the last two
+// instantiated for single-text, one-symbol launches with 2 or 4 chains; null
+// otherwise)
+template <int FMT, int ALPHA, bool BATCH, bool TRACK, int R = 1>
+KernelFn pick_variant(int mode, uint32_t bx, uint32_t C) {
+    if (mode == MODE_OPT || mode == MODE_H16) {
+        if constexpr (!BATCH && R == 1) {
+            if (mode == MODE_OPT) {
+                if (C == 2) return bx == 16 ? scan_kernel<FMT, ALPHA, MODE_OPT, 16, 2, BATCH, TRACK, R>
+                                            : scan_kernel<FMT, ALPHA, MODE_OPT, 32, 2, BATCH, TRACK, R>;
+                if (C == 4) return bx == 16 ? scan_kernel<FMT, ALPHA, MODE_OPT, 16, 4, BATCH, TRACK, R>
+                                            : scan_kernel<FMT, ALPHA, MODE_OPT, 32, 4, BATCH, TRACK, R>;
+            } else {
+                if (C == 2) return bx == 16 ? scan_kernel<FMT, ALPHA, MODE_H16, 16, 2, BATCH, TRACK, R>
+                                            : scan_kernel<FMT, ALPHA, MODE_H16, 32, 2, BATCH, TRACK, R>;
+                if (C == 4) return bx == 16 ? scan_kernel<FMT, ALPHA, MODE_H16, 16, 4, BATCH, TRACK, R>
+                                            : scan_kernel<FMT, ALPHA, MODE_H16, 32, 4, BATCH, TRACK, R>;
+            }
+        }
+        return nullptr;
+    }
+    return mode == MODE_HYBRID ? pick_shape<FMT, ALPHA, MODE_HYBRID, BATCH, TRACK, R>(bx, C)
+                               : pick_shape<FMT, ALPHA, MODE_SMEM, BATCH, TRACK, R>(bx, C);
 }
 
 // defined in the scan_k_*.cu translation units (compiled in parallel)
 #define AC_KERNEL_SET(name)                                                              \
-    KernelFn kernels_##name##_single_plain(bool hybrid, uint32_t bx, uint32_t C);       \
-    KernelFn kernels_##name##_single_track(bool hybrid, uint32_t bx, uint32_t C);       \
-    KernelFn kernels_##name##_batch_plain(bool hybrid, uint32_t bx, uint32_t C);        \
-    KernelFn kernels_##name##_batch_track(bool hybrid, uint32_t bx, uint32_t C);        \
-    inline KernelFn kernels_##name(bool batch, bool track, bool hybrid, uint32_t bx, uint32_t C) { \
-        if (batch) return track ? kernels_##name##_batch_track(hybrid, bx, C) : kernels_##name##_batch_plain(hybrid, bx, C); \
-        return track ? kernels_##name##_single_track(hybrid, bx, C) : kernels_##name##_single_plain(hybrid, bx, C); \
+    KernelFn kernels_##name##_single_plain(int mode, uint32_t bx, uint32_t C);       \
+    KernelFn kernels_##name##_single_track(int mode, uint32_t bx, uint32_t C);       \
+    KernelFn kernels_##name##_batch_plain(int mode, uint32_t bx, uint32_t C);        \
+    KernelFn kernels_##name##_batch_track(int mode, uint32_t bx, uint32_t C);        \
+    inline KernelFn kernels_##name(bool batch, bool track, int mode, uint32_t bx, uint32_t C) { \
+        if (batch) return track ? kernels_##name##_batch_track(mode, bx, C) : kernels_##name##_batch_plain(mode, bx, C); \
+        return track ? kernels_##name##_single_track(mode, bx, C) : kernels_##name##_single_plain(mode, bx, C); \
     }
 AC_KERNEL_SET(u8_acgt)
 AC_KERNEL_SET(u8_map)
 AC_KERNEL_SET(packed)
 #undef AC_KERNEL_SET
+// two-symbol table (single-text launches)
+KernelFn kernels_u8_acgt_single_plain_r2(int mode, uint32_t bx, uint32_t C);
+KernelFn kernels_u8_acgt_single_track_r2(int mode, uint32_t bx, uint32_t C);
+KernelFn kernels_packed_single_plain_r2(int mode, uint32_t bx, uint32_t C);
+KernelFn kernels_packed_single_track_r2(int mode, uint32_t bx, uint32_t C);
 
 }  // namespace kern
 }  // namespace acgb

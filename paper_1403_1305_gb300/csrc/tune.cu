@@ -1,5 +1,6 @@
-// ac_tune: pick the scan configuration (row length, threads per CTA, chains
-// per thread) for an automaton by timing candidates on a real text.
+// ac_tune: pick the scan configuration (CTA shape, shared-memory table size,
+// symbols per lookup, row length) for an automaton by timing candidates on a
+// real text, one coordinate at a time.
 #include "ac_internal.h"
 
 using namespace acgb;
@@ -78,7 +79,20 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
             best = c;
         }
     }
-    // 3. row length
+    // 3. symbols per lookup (when the two-symbol table applies to this format)
+    if (scan_stride(a, fmt, 2) == 2) {
+        base = best;
+        for (uint32_t stride = 1; stride <= 2 && rc == AC_OK; ++stride) {
+            ac_scan_config c = base;
+            c.stride = stride;
+            const float ms = timeit(c);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    // 4. row length
     base = best;
     for (int li = 0; li < 2 && rc == AC_OK; ++li) {
         ac_scan_config c = base;

@@ -280,3 +280,41 @@ def test_tune_and_table_caps():
     assert chosen["threads"] in (256, 512) and chosen["chains"] in (1, 2, 4)
     assert A.ac_get_scan_config(a) == chosen
     same(A.ac_scan(a, d), want)
+
+
+@pytest.mark.parametrize("cap", [64, 1024, 16 << 10])
+def test_optimistic_placement_repairs(cap):
+    """AC_PLACE_OPT with a small power-of-two prefix: many stages reach a
+    state beyond it and are walked again; the result stays exact. Chains = 1
+    has no optimistic kernel and runs the hybrid one."""
+    rng = np.random.default_rng(700 + cap)
+    for i in range(60):
+        alph = (b"ACGT", b"ab", b"ACDEFGHIKLMNPQRSTVWY")[i % 3]
+        text, pats = workloads.tiny_case(rng, alph, max_n=3000, max_p=40, max_len=16,
+                                         other_frac=0.03 if i % 4 == 0 else 0.0)
+        K = 1 + (i % 3) if len(pats) >= 3 else 1
+        a = A.ac_build(pats, num_subsets=K, placement=A.AC_PLACE_OPT, smem_table_bytes=cap, stride=1)
+        A.ac_set_scan_config(a, **[dict(row_len=64, threads=64, chains=2, stage_bytes=16),
+                                   dict(row_len=128, threads=128, chains=4),
+                                   dict(row_len=96, threads=64, chains=1)][i % 3])
+        want = oracle.scan(pats, text)
+        same(A.ac_scan(a, text), want)
+        if alph == b"ACGT" and not np.any(~np.isin(text, np.frombuffer(b"ACGT", np.uint8))) and a_is_acgt(pats):
+            same(A.ac_scan(a, workloads.pack2(text), n=text.size, fmt=A.AC_PACKED2), want)
+
+
+def a_is_acgt(pats):
+    return set(b"".join(pats)) == set(b"ACGT")
+
+
+def test_optimistic_placement_chosen_for_many_subsets():
+    """Config 2 at 16 subsets: the automatic placement reads a power-of-two
+    prefix optimistically; the same result as the hybrid placement."""
+    w = workloads.config2(n=8 << 20)
+    want = oracle.Machine(w.patterns).scan_mt(w.text, THREADS)
+    d = torch.from_numpy(w.text).cuda()
+    for placement in (A.AC_PLACE_AUTO, A.AC_PLACE_OPT, A.AC_PLACE_HYBRID):
+        a = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=16, placement=placement)
+        for cfg in (dict(stride=1), dict(stride=1, stage_bytes=32), dict(stride=1, chains=4)):
+            A.ac_set_scan_config(a, **cfg)
+            same(A.ac_scan(a, d), want)

@@ -184,3 +184,98 @@ def test_failure_less_machine_tables():
     a = A.ac_build([b"HE", b"HIS", b"SHE", b"HERS"], device=-1, machine=A.AC_MACHINE_PFAC)
     assert pfac_walk(a, b"USHERS").tolist() == [[3, 0], [3, 2], [5, 3]]
     assert A.ac_stats(a)["states"] == oracle.Machine([b"HE", b"HIS", b"SHE", b"HERS"], False).num_states
+
+
+def walk2(a, text):
+    """Scan `text` two symbols per lookup with the library's two-symbol host
+    tables (pairs holding a byte outside the alphabet, and a ragged last
+    symbol, go through the one-symbol table), in numpy."""
+    res = []
+    for k in range(A.ac_stats(a)["num_subsets"]):
+        v = A.ac_subset(a, k)
+        T, T2, off, ids, sym = v["table"], v["table2"], v["out_off"], v["out_ids"], v["symbol_of_byte"]
+        tb = np.frombuffer(text, np.uint8).tolist() if isinstance(text, bytes) else list(text)
+        s = 0
+
+        def step(s, i):
+            c = sym[tb[i]]
+            e = int(T[s, c]) if c < 4 else 0
+            if e >> 31:
+                res.extend((i, int(j)) for j in ids[off[e & 0x7FFFFFFF]:off[(e & 0x7FFFFFFF) + 1]])
+            return e & 0x7FFFFFFF
+
+        i = 0
+        while i < len(tb):
+            c1 = sym[tb[i]]
+            c2 = sym[tb[i + 1]] if i + 1 < len(tb) else 4
+            if c1 < 4 and c2 < 4:
+                e = int(T2[s, c1 + 4 * c2])
+                mid = int(T[s, c1]) & 0x7FFFFFFF
+                assert bool(e & (1 << 30)) == (off[mid + 1] > off[mid])
+                if e & (1 << 30):
+                    res.extend((i, int(j)) for j in ids[off[mid]:off[mid + 1]])
+                s = e & 0x3FFFFFFF
+                assert bool(e >> 31) == (off[s + 1] > off[s])
+                if e >> 31:
+                    res.extend((i + 1, int(j)) for j in ids[off[s]:off[s + 1]])
+                i += 2
+            else:
+                s = step(s, i)
+                i += 1
+    res.sort()
+    return np.asarray(res, dtype=np.uint32).reshape(-1, 2)
+
+
+def test_two_symbol_tables_match_oracle():
+    """The two-symbol table (built automatically for 4-letter alphabets):
+    a pair-wise walk over it gives the oracle's matches, including texts of
+    odd length and bytes outside the alphabet."""
+    rng = np.random.default_rng(77)
+    checked = 0
+    for i in range(300):
+        text, pats = workloads.tiny_case(rng, b"ACGT", max_n=81, max_p=9, max_len=7,
+                                         other_frac=0.1 if i % 3 == 0 else 0.0)
+        K = 1 + i % 2 if len(pats) >= 2 else 1
+        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K, device=-1)
+        assert A.ac_subset(a, 0)["table2"] is not None
+        assert A.ac_stats(a)["table2_bytes"] == 4 * A.ac_stats(a)["table_bytes"]
+        assert np.array_equal(walk2(a, text), oracle.scan(pats, text)[0]), (i, pats, bytes(text))
+        checked += 1
+    assert checked == 300
+
+
+def test_two_symbol_table_options():
+    pats = [b"ACG", b"GT", b"TTA"]
+    assert A.ac_subset(A.ac_build(pats, alphabet="ACGT", device=-1, stride=1), 0)["table2"] is None
+    assert A.ac_stats(A.ac_build(pats, alphabet="ACGT", device=-1, stride=1))["table2_bytes"] == 0
+    assert A.ac_subset(A.ac_build(pats, alphabet="ACGT", device=-1, stride=2), 0)["table2"] is not None
+    assert A.ac_subset(A.ac_build([b"ab", b"ba"], device=-1), 0)["table2"] is None       # 2 letters
+    assert A.ac_subset(A.ac_build(pats, alphabet="ACGT", device=-1, machine=A.AC_MACHINE_PFAC), 0)["table2"] is None
+    for kw in (dict(alphabet="ACGTN", stride=2), dict(alphabet="ACGT", stride=3),
+               dict(alphabet="ACGT", stride=2, machine=A.AC_MACHINE_PFAC)):
+        with pytest.raises(A.AcError) as e:
+            A.ac_build(pats, device=-1, **kw)
+        assert e.value.code == A.AC_EINVAL
+    a = A.ac_build(pats, alphabet="ACGT", device=-1, stride=1)
+    with pytest.raises(A.AcError):
+        A.ac_set_scan_config(a, stride=2)
+    with pytest.raises(A.AcError):
+        A.ac_set_scan_config(a, stride=5)
+    A.ac_set_scan_config(a, stride=1)
+
+
+def test_sixteen_bit_prefix():
+    """The 16-bit prefix holds (next << 1) | output bit for the longest
+    breadth-first prefix of rows whose next states fit 15 bits."""
+    w = workloads.config2(n=1 << 20, P=3000)
+    a = A.ac_build(w.patterns, alphabet="ACGT", device=-1)
+    v = A.ac_subset(a, 0)
+    T, T16 = v["table"], v["table16"]
+    r = T16.shape[0]
+    assert 0 < r < v["states"]
+    assert np.array_equal(T16.astype(np.uint32) >> 1, T[:r] & 0x7FFFFFFF)
+    assert np.array_equal(T16.astype(np.uint32) & 1, T[:r] >> 31)
+    assert (T[r] & 0x7FFFFFFF).max() > 0x7FFF      # the next row does not fit
+    assert A.ac_subset(A.ac_build([b"ab", b"ba"], device=-1), 0)["table16"] is None
+    small = A.ac_subset(A.ac_build([b"ACGT", b"GA"], alphabet="ACGT", device=-1), 0)
+    assert small["table16"].shape[0] == small["states"]
