@@ -669,8 +669,12 @@ def main():
                        "patterns": len(w.patterns), "pattern_len": [16, 64], "subsets": args.subsets,
                        "states": st["states"], "table_bytes": st["table_bytes"], "smem_states": st["smem_states"],
                        "matches": M, "build_ms": build_s * 1e3, "parallelism": f"replicas{world}",
-                       "l2": "text (256 MiB) larger than L2 (129 MB): no flush between steps",
-                       "scan_config": A.ac_get_scan_config(a)},
+                       "l2": (f"text ({nbytes / 2**20:.0f} MiB) larger than L2 (129 MB): no flush between steps"
+                              if nbytes > 129e6 else f"text ({nbytes / 2**20:.0f} MiB) fits in L2: a warm-L2 figure"),
+                       "scan_config": A.ac_get_scan_config(a),
+                       "scan_placement": {0: "auto", 1: "smem", 2: "hybrid", 3: "global", 4: "optimistic prefix",
+                                          5: "16-bit prefix"}.get(st["scan_placement"], str(st["scan_placement"])),
+                       "symbols_per_lookup": st["scan_stride"]},
             "roofline": roofline, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_note": "own kernels per step: scan, error mark, one-CTA key sort + record conversion "
