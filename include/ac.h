@@ -109,12 +109,14 @@ typedef struct {
     int32_t device;        /* CUDA device ordinal; -1 builds on the host only (inspection, no scans) */
     uint32_t smem_table_bytes; /* cap on table bytes held in shared memory per CTA; 0 = as much as fits */
     int32_t machine;           /* AC_MACHINE_DFA (default) or AC_MACHINE_PFAC; the results are the same */
-    uint32_t stride;           /* symbols per table lookup the DFA machine is built for: 0 = automatic (1 and
-                                  2 for a 4-letter alphabet, else 1), 1 = one-symbol table only, 2 = also the
-                                  two-symbol table (4-letter alphabets and the DFA machine only, else
-                                  AC_EINVAL). The two-symbol table composes two transitions of the one-symbol
-                                  table (16 columns per state, 4x its memory) so a scan does one dependent
-                                  lookup per two text symbols; results are the same. */
+    uint32_t stride;           /* symbols per table lookup the DFA machine is built for: 0 = automatic (the
+                                  two-symbol table too for a 4-letter alphabet whose subsets are small enough
+                                  for a scan to choose it: most visits within the first ~2,048 states, as
+                                  estimated from the patterns' letter frequencies), 1 = one-symbol table only,
+                                  2 = always the two-symbol table too (4-letter alphabets and the DFA machine
+                                  only, else AC_EINVAL). The two-symbol table composes two transitions of the
+                                  one-symbol table (16 columns per state, 4x its memory) so a scan does one
+                                  dependent lookup per two text symbols; results are the same. */
 } ac_build_opts;
 
 typedef struct {

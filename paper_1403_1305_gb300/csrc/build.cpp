@@ -380,7 +380,7 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
                             : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
                 if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA) build_tail_mass(a->subs[k], sigma, prob);
                 if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA && sigma == 4) build_table16(a->subs[k]);
-                if (rc[k] == AC_OK && want2 && a->subs[k].states < kMaxStates2) build_table2(a->subs[k]);
+                if (rc[k] == AC_OK && stride == 2 && a->subs[k].states < kMaxStates2) build_table2(a->subs[k]);
             } catch (const std::bad_alloc &) {
                 rc[k] = AC_ENOMEM;
                 why[k] = "host allocation failed";
@@ -396,6 +396,16 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
     }
     for (uint32_t k = 0; k < K; ++k)
         if (rc[k] != AC_OK) return set_error(rc[k], "ac_build: subset %u: %s", k, why[k].c_str());
+    if (want2 && stride == 0) {
+        // automatic: only where a scan could choose it, i.e. a two-symbol
+        // prefix of about 2,048 rows (what shared memory holds) keeps nearly
+        // every visit (the same estimate the scan's choice uses)
+        double worst = 0;
+        for (auto &S : a->subs) worst = std::max(worst, S.tail_mass[11]);
+        if (worst <= 0.02)
+            for (auto &S : a->subs)
+                if (S.states < kMaxStates2) build_table2(S);
+    }
     a->has_table2 = want2;
     for (auto &S : a->subs) a->has_table2 = a->has_table2 && !S.table2.empty();
     if (stride == 2 && !a->has_table2)

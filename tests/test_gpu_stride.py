@@ -65,7 +65,7 @@ def test_random_small_cases(cfg):
         text, pats = workloads.tiny_case(rng, b"ACGT", max_n=900, max_p=16, max_len=20,
                                          other_frac=0.03 if i % 4 == 0 else 0.0)
         K = 1 + i % 3 if len(pats) >= 3 else 1
-        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K,
+        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K, stride=2,
                        smem_table_bytes=(0, 64, 2048)[i % 3])
         both_strides(a, np.asarray(text), oracle.scan(pats, text), **CONFIGS[cfg])
 
@@ -87,7 +87,7 @@ def test_isolated_matches_at_even_and_odd_ends(K):
         want = oracle.scan(pats, text)
         assert want[0].shape[0] >= 20
         assert len(set((want[0][:, 0] % 2).tolist())) == 2
-        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K)
+        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K, stride=2)
         both_strides(a, text, want, row_len=512, threads=128, chains=2)
         both_strides(a, text, want)
 
@@ -99,7 +99,7 @@ def test_match_at_every_position(K):
     rng = np.random.default_rng(620 + K)
     for n in (7, 64, 1001, 30_000):
         text = workloads.dna_text(rng, n)
-        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K)
+        a = A.ac_build(pats, alphabet="ACGT", num_subsets=K, stride=2)
         both_strides(a, text, oracle.scan(pats, text), row_len=64, threads=64, chains=2)
 
 
@@ -112,7 +112,7 @@ def test_global_placement_and_bytes_outside_the_alphabet():
         t[rng.random(t.size) < 0.002] = other[0]
         want = oracle.scan(pats, t)
         for placement in (A.AC_PLACE_AUTO, A.AC_PLACE_GLOBAL, A.AC_PLACE_HYBRID):
-            a = A.ac_build(pats, alphabet="ACGT", placement=placement, smem_table_bytes=4096)
+            a = A.ac_build(pats, alphabet="ACGT", placement=placement, smem_table_bytes=4096, stride=2)
             both_strides(a, t, want, packed=False, row_len=256, threads=128, chains=2)
 
 
@@ -122,8 +122,25 @@ def test_ragged_lengths_u8_and_packed():
         text = workloads.dna_text(rng, n)
         src = workloads.dna_text(rng, 64)
         pats = workloads.draw_patterns(rng, [src, text], 16, 1, 7, 0.6, ACGT)
-        a = A.ac_build(pats, alphabet="ACGT")
+        a = A.ac_build(pats, alphabet="ACGT", stride=2)
         both_strides(a, text, oracle.scan(pats, text), row_len=64, threads=32, chains=2, stage_bytes=16)
+
+
+def test_automatic_stride():
+    """Two symbols per lookup by default only where they pay: config 2 at 16
+    subsets (built and chosen), not at one machine (not even built)."""
+    w = workloads.config2(n=4 << 20)
+    a16 = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=16)
+    st = A.ac_stats(a16)
+    assert st["table2_bytes"] > 0 and st["scan_stride"] == 2
+    a1 = A.ac_build(w.patterns, alphabet="ACGT")
+    st = A.ac_stats(a1)
+    assert st["table2_bytes"] == 0 and st["scan_stride"] == 1
+    assert st["scan_placement"] == A.AC_PLACE_HYBRID16
+    want = oracle.Machine(w.patterns).scan_mt(w.text, THREADS)
+    d = torch.from_numpy(w.text).cuda()
+    same(A.ac_scan(a16, d), want)
+    same(A.ac_scan(a1, d), want)
 
 
 def test_stride_selection_and_errors():
@@ -135,7 +152,7 @@ def test_stride_selection_and_errors():
     # (asked for 2: AC_EINVAL), packed text with 2
     low = [p.lower() for p in pats]
     tl = np.frombuffer(bytes(text).lower(), np.uint8)
-    a = A.ac_build(low, alphabet="acgt")
+    a = A.ac_build(low, alphabet="acgt", stride=2)
     same(A.ac_scan(a, tl), want)
     A.ac_set_scan_config(a, stride=2)
     with pytest.raises(A.AcError) as e:
@@ -150,7 +167,7 @@ def test_stride_selection_and_errors():
     # placement SMEM: the one-symbol table fits, the two-symbol one does not,
     # so the automatic stride falls back to 1
     w = workloads.config2(n=1 << 20, P=200)
-    a = A.ac_build(w.patterns, alphabet="ACGT", placement=A.AC_PLACE_SMEM)
+    a = A.ac_build(w.patterns, alphabet="ACGT", placement=A.AC_PLACE_SMEM, stride=2)
     st = A.ac_stats(a)
     assert st["table_bytes"] < (128 << 10) and st["table2_bytes"] > (232 << 10)
     same(A.ac_scan(a, w.text), oracle.scan(w.patterns, w.text))
@@ -169,7 +186,7 @@ def cfg2_small():
 def test_config2_16MiB_both_strides(cfg2_small, K):
     w = cfg2_small
     want = oracle.Machine(w.patterns).scan_mt(w.text, THREADS)
-    a = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=K)
+    a = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=K, stride=2)
     d = torch.from_numpy(w.text).cuda()
     dp = torch.from_numpy(workloads.pack2(w.text)).cuda()
     for stride in (1, 2):
@@ -185,7 +202,7 @@ def test_config2_full_size_embedded_matches():
     rng = np.random.default_rng(660)
     text = workloads.embed(rng, w.text.copy(), w.patterns, 100_000)
     want = oracle.Machine(w.patterns).scan_mt(text, THREADS)
-    a = A.ac_build(w.patterns, alphabet="ACGT")
+    a = A.ac_build(w.patterns, alphabet="ACGT", stride=2)
     d = torch.from_numpy(text).cuda()
     for stride in (2, 1):
         A.ac_set_scan_config(a, stride=stride)
