@@ -223,7 +223,7 @@ def run_reference(args):
 # ---------------------------------------------------------------- our arm
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("scan_kernel.cuh", "scan.cu"):
+    for name in ("scan_kernel.cuh", "scan_lean.cuh", "scan.cu"):
         with open(os.path.join(ROOT, "paper_1403_1305_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -656,7 +656,8 @@ def main():
     roofline = {"bound": bound, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": ncu_traffic(key),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "scan_kernel (+ memsets, error mark)", "kernel_ms": scan_s * 1e3,
+                "kernel": ("lean_kernel" if st["scan_kernel"] == A.AC_KERNEL_LEAN else "scan_kernel")
+                          + " (+ memsets, error mark)", "kernel_ms": scan_s * 1e3,
                 "algorithmic_bytes_per_launch": nbytes,
                 "roofline_ms": max(t_hbm, t_lookup) * 1e3,
                 "frac_of_roofline_time": max(t_hbm, t_lookup) / scan_s,
@@ -674,7 +675,8 @@ def main():
                        "scan_config": A.ac_get_scan_config(a),
                        "scan_placement": {0: "auto", 1: "smem", 2: "hybrid", 3: "global", 4: "optimistic prefix",
                                           5: "16-bit prefix"}.get(st["scan_placement"], str(st["scan_placement"])),
-                       "symbols_per_lookup": st["scan_stride"]},
+                       "symbols_per_lookup": st["scan_stride"],
+                       "scan_kernel": {1: "general", 2: "lean"}.get(st["scan_kernel"], str(st["scan_kernel"]))},
             "roofline": roofline, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_note": "own kernels per step: scan, error mark, one-CTA key sort + record conversion "

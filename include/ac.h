@@ -145,6 +145,8 @@ typedef struct {
     int32_t scan_placement;  /* the table placement (AC_PLACE_SMEM, _HYBRID, _OPT or _HYBRID16) and symbols per */
     uint32_t scan_stride;    /* lookup a scan of byte text would use with the current configuration; -1 and 0
                                 when not applicable (host-only automaton, failure-less machine) */
+    int32_t scan_kernel;     /* AC_KERNEL_GENERAL or AC_KERNEL_LEAN: the kernel such a scan runs (-1 when not
+                                applicable) */
 } ac_stats_t;
 
 /* Read-only host view of one subset machine (valid until ac_free). States are
@@ -172,15 +174,22 @@ typedef struct {
        not empty */
     const uint16_t *table16;
     uint32_t rows16;
+    /* escape-coded 16-bit prefix (4-letter alphabets, DFA machine; NULL otherwise), the lean kernel's shared-
+       memory table: rows [0, rows_e16) (at most 32,768); table_e16[s*4 + c] = the next state when it is
+       below 65,535 and its output is empty, else 65,535 (the lookup then reads table[]) */
+    const uint16_t *table_e16;
+    uint32_t rows_e16;
 } ac_subset_view;
 
 /* Scan configuration (ac_set_scan_config / ac_tune). Zero fields = defaults. */
 typedef struct {
     uint32_t row_len;     /* text symbols per chain (rounded up to 32 bytes of text) */
-    uint32_t threads;     /* threads per CTA (multiple of 32, <= 512) */
+    uint32_t threads;     /* threads per CTA (multiple of 32; <= 512 for the general kernel; 512, 768 or
+                             1024 for the lean one) */
     uint32_t chains;      /* independent chains per thread: 1, 2 or 4 */
     uint32_t ctas;        /* persistent grid size; 0 = one per SM */
-    uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains) */
+    uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains; the
+                             lean kernel always uses 16) */
     uint32_t smem_table_bytes; /* cap on table bytes staged in shared memory for this scan (0 = the
                                   automaton's cap or as much as fits); a smaller table leaves more of the
                                   SM's memory to L1, which caches the rows a skewed text visits most */
@@ -188,7 +197,18 @@ typedef struct {
                              table and the text is ACGT bytes or packed, else 1), 1, or 2 (AC_EINVAL at scan
                              time when the two-symbol table or a suitable format is missing). Batched scans
                              use 1. */
+    uint32_t kernel;      /* AC_KERNEL_*: which scan kernel a single-text scan runs (results are the same) */
 } ac_scan_config;
+
+/* Scan kernels (ac_scan_config.kernel). */
+#define AC_KERNEL_AUTO 0    /* the lean kernel where it applies, else the general one */
+#define AC_KERNEL_GENERAL 1 /* every table placement, alphabet and stride; threads <= 512, chains 1, 2 or 4 */
+#define AC_KERNEL_LEAN 2    /* one-symbol scans of a 4-letter machine over ACGT bytes or packed text
+                               (placement AUTO, SMEM or HYBRID16): the whole table in shared memory when it
+                               fits, else an escape-coded 16-bit breadth-first prefix with the rest read
+                               through L2; 16-byte stages; (threads, chains) in {(1024, 4), (1024, 2),
+                               (768, 4), (512, 4)}, default (1024, 4). AC_EINVAL at scan time when it does
+                               not apply. */
 
 /* ------------------------------------------------------------ automaton */
 

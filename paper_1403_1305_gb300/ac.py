@@ -27,6 +27,7 @@ AC_HOST, AC_DEVICE = 0, 1
 AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL, AC_PLACE_OPT, AC_PLACE_HYBRID16 = 0, 1, 2, 3, 4, 5
 AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
 AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
+AC_KERNEL_AUTO, AC_KERNEL_GENERAL, AC_KERNEL_LEAN = 0, 1, 2
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
@@ -64,7 +65,7 @@ class ac_stats_t(C.Structure):
                 ("output_entries", C.c_uint64), ("smem_states", C.c_uint64), ("build_ms", C.c_double),
                 ("upload_ms", C.c_double), ("device", C.c_int32), ("row_len", C.c_uint32),
                 ("threads", C.c_uint32), ("chains", C.c_uint32), ("table2_bytes", C.c_uint64),
-                ("scan_placement", C.c_int32), ("scan_stride", C.c_uint32)]
+                ("scan_placement", C.c_int32), ("scan_stride", C.c_uint32), ("scan_kernel", C.c_int32)]
 
 
 class ac_subset_view(C.Structure):
@@ -73,12 +74,14 @@ class ac_subset_view(C.Structure):
                 ("fail", C.POINTER(C.c_uint32)), ("depth", C.POINTER(C.c_uint32)),
                 ("out_off", C.POINTER(C.c_uint32)), ("out_ids", C.POINTER(C.c_uint32)),
                 ("symbol_of_byte", C.POINTER(C.c_uint8)), ("table2", C.POINTER(C.c_uint32)),
-                ("table16", C.POINTER(C.c_uint16)), ("rows16", C.c_uint32)]
+                ("table16", C.POINTER(C.c_uint16)), ("rows16", C.c_uint32),
+                ("table_e16", C.POINTER(C.c_uint16)), ("rows_e16", C.c_uint32)]
 
 
 class ac_scan_config(C.Structure):
     _fields_ = [("row_len", C.c_uint32), ("threads", C.c_uint32), ("chains", C.c_uint32), ("ctas", C.c_uint32),
-                ("stage_bytes", C.c_uint32), ("smem_table_bytes", C.c_uint32), ("stride", C.c_uint32)]
+                ("stage_bytes", C.c_uint32), ("smem_table_bytes", C.c_uint32), ("stride", C.c_uint32),
+                ("kernel", C.c_uint32)]
 
 
 class ac_batch_item(C.Structure):
@@ -286,12 +289,14 @@ def ac_subset(a: Automaton, k: int) -> dict:
             "out_off": out_off, "out_ids": arr(v.out_ids, int(out_off[-1])),
             "symbol_of_byte": arr(v.symbol_of_byte, 256, np.uint8),
             "table2": arr(v.table2, S * 16).reshape(S, 16) if v.table2 else None,
-            "table16": arr(v.table16, v.rows16 * 4, np.uint16).reshape(-1, 4) if v.table16 else None}
+            "table16": arr(v.table16, v.rows16 * 4, np.uint16).reshape(-1, 4) if v.table16 else None,
+            "table_e16": arr(v.table_e16, v.rows_e16 * 4, np.uint16).reshape(-1, 4) if v.table_e16 else None}
 
 
 def ac_set_scan_config(a: Automaton, row_len: int = 0, threads: int = 0, chains: int = 0, ctas: int = 0,
-                       stage_bytes: int = 0, smem_table_bytes: int = 0, stride: int = 0):
-    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes, smem_table_bytes, stride)
+                       stage_bytes: int = 0, smem_table_bytes: int = 0, stride: int = 0,
+                       kernel: int = AC_KERNEL_AUTO):
+    cfg = ac_scan_config(row_len, threads, chains, ctas, stage_bytes, smem_table_bytes, stride, kernel)
     _check(lib().ac_set_scan_config(a.h, C.byref(cfg)), "ac_set_scan_config")
 
 

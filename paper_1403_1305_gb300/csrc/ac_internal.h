@@ -20,6 +20,10 @@ constexpr uint32_t kMissing = 0x7fffffffu;  // failure-less table: no transition
 constexpr uint32_t kFlag1 = 0x40000000u;
 constexpr uint32_t kStateMask2 = 0x3fffffffu;
 constexpr uint32_t kMaxStates2 = 1u << 28;  // s*16 + column must fit 32 bits
+// escape-coded 16-bit prefix (lean scan): entry = next state, or kEsc16 when the
+// next state has an output or does not fit 16 bits (read the 32-bit table)
+constexpr uint32_t kEsc16 = 0xffffu;
+constexpr uint32_t kRowsE16 = 1u << 15;  // rows built (256 KB): more than shared memory holds
 
 // ---------------------------------------------------------------- host machine
 struct HostSubset {
@@ -40,6 +44,10 @@ struct HostSubset {
     // 15 bits; entry = (next state << 1) | 1 when its output is not empty
     std::vector<uint16_t> table16;
     uint32_t rows16 = 0;
+    // escape-coded 16-bit prefix (sigma = 4): rows [0, rows_e16), entry =
+    // next state, or kEsc16 when that state has an output or is >= kEsc16
+    std::vector<uint16_t> table_e16;
+    uint32_t rows_e16 = 0;
 };
 
 // Device descriptor of one subset machine (array in device memory, one per subset).
@@ -48,6 +56,8 @@ struct SubsetDev {
     const uint32_t *table2;   // states * 16 (two-symbol table) or null
     const uint16_t *table16;  // rows16 * 4 (16-bit prefix) or null
     uint32_t rows16;
+    const uint16_t *table_e16;  // rows_e16 * 4 (escape-coded 16-bit prefix) or null
+    uint32_t rows_e16;
     const uint32_t *out_off;  // states + 1
     const uint32_t *out_ids;
     uint32_t states;
@@ -73,7 +83,7 @@ struct BatchTileDev {
 
 struct DeviceSubset {
     uint32_t *table = nullptr, *out_off = nullptr, *out_ids = nullptr, *table2 = nullptr;
-    uint16_t *table16 = nullptr;
+    uint16_t *table16 = nullptr, *table_e16 = nullptr;
 };
 
 }  // namespace acgb
@@ -137,7 +147,10 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
 // under configuration cfg (defaults filled in): kernel mode (the kernels'
 // MODE_* values), table rows staged in shared memory, words of shared memory
 // for the table, dynamic shared memory bytes.
+// table placements of the lean kernel (ScanPlan::mode when ScanPlan::lean)
+enum { kLeanSmem32 = 0, kLeanE16 = 1 };
 struct ScanPlan {
+    bool lean = false;  // the lean kernel (mode = kLeanSmem32 or kLeanE16)
     int mode = 0;
     uint32_t stride = 1;
     uint32_t smem_rows = 0;

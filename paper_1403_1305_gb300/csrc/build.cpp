@@ -283,6 +283,22 @@ void build_table16(HostSubset &S) {
     }
 }
 
+// Escape-coded 16-bit prefix of a 4-letter machine (the lean scan's shared-
+// memory table): entry = next state when it is below kEsc16 and its output is
+// empty, else kEsc16, which sends the lookup to the 32-bit table in global
+// memory (whose entry carries the output flag). Every row can be held this
+// way, so the prefix is as long as shared memory allows (at most kRowsE16).
+void build_table_e16(HostSubset &S) {
+    const uint32_t rows = std::min<uint32_t>(S.states, kRowsE16);
+    S.rows_e16 = rows;
+    S.table_e16.resize((size_t)rows * 4);
+    for (size_t i = 0; i < S.table_e16.size(); ++i) {
+        const uint32_t e = S.table[i];
+        const uint32_t next = e & kStateMask;
+        S.table_e16[i] = (uint16_t)((next < kEsc16 && !(e & kFlag)) ? next : kEsc16);
+    }
+}
+
 // Visit estimate for the placement choice: the probability of each state's
 // string under i.i.d. letters with probabilities prob[] (a goto child's is
 // its parent's times its letter's), summed over the states at or beyond each
@@ -379,7 +395,10 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
                             ? build_subset_pfac(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k])
                             : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
                 if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA) build_tail_mass(a->subs[k], sigma, prob);
-                if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA && sigma == 4) build_table16(a->subs[k]);
+                if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA && sigma == 4) {
+                    build_table16(a->subs[k]);
+                    build_table_e16(a->subs[k]);
+                }
                 if (rc[k] == AC_OK && stride == 2 && a->subs[k].states < kMaxStates2) build_table2(a->subs[k]);
             } catch (const std::bad_alloc &) {
                 rc[k] = AC_ENOMEM;

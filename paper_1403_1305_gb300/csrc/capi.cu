@@ -127,6 +127,7 @@ static void free_device(ac_automaton *a) {
         cudaFree(d.table);
         cudaFree(d.table2);
         cudaFree(d.table16);
+        cudaFree(d.table_e16);
         cudaFree(d.out_off);
         cudaFree(d.out_ids);
     }
@@ -161,8 +162,15 @@ static int upload(ac_automaton *a) {
             CK(cudaMalloc(&d.table16, h.table16.size() * 2), "ac_build: 16-bit prefix");
             CK(cudaMemcpy(d.table16, h.table16.data(), h.table16.size() * 2, cudaMemcpyHostToDevice), "ac_build: copy");
         }
+        if (!h.table_e16.empty()) {
+            CK(cudaMalloc(&d.table_e16, h.table_e16.size() * 2), "ac_build: escape-coded 16-bit prefix");
+            CK(cudaMemcpy(d.table_e16, h.table_e16.data(), h.table_e16.size() * 2, cudaMemcpyHostToDevice),
+               "ac_build: copy");
+        }
         SubsetDev &s = a->h_desc[k];
         s.table = d.table;
+        s.table_e16 = d.table_e16;
+        s.rows_e16 = d.table_e16 ? h.rows_e16 : 0;
         s.table2 = d.table2;
         s.table16 = d.table16;
         s.rows16 = d.table16 ? h.rows16 : 0;
@@ -279,8 +287,12 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
     if (rc == AC_OK && a->device >= 0) {
         rc = upload(a);
         if (rc == AC_OK && a->placement == AC_PLACE_SMEM) {
+            // the general kernel's room (the lean kernel steps aside when its own is smaller)
             ac_scan_config c{};
+            const ac_scan_config user = a->cfg;
+            a->cfg.kernel = AC_KERNEL_GENERAL;
             default_config(a, 1, AC_U8, &c);
+            a->cfg = user;
             int limit = scan_smem_limit(a->device);
             uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
             if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
@@ -322,14 +334,20 @@ int ac_stats(const ac_automaton *a, ac_stats_t *o) {
     }
     // kernel modes of the plan: 0 all rows, 1 hybrid, 2 optimistic prefix, 3 16-bit prefix
     static const int32_t kPlacementOfMode[4] = {AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_OPT, AC_PLACE_HYBRID16};
-    o->scan_placement = planned ? kPlacementOfMode[plan.mode & 3] : -1;
+    o->scan_placement = !planned ? -1
+                        : plan.lean ? (plan.mode == kLeanSmem32 ? AC_PLACE_SMEM : AC_PLACE_HYBRID16)
+                                    : kPlacementOfMode[plan.mode & 3];
     o->scan_stride = planned ? plan.stride : 0;
+    o->scan_kernel = !planned ? -1 : plan.lean ? AC_KERNEL_LEAN : AC_KERNEL_GENERAL;
     for (auto &s : a->subs) {
         o->states += s.states;
         o->table_bytes += (uint64_t)s.table.size() * 4;
         o->output_entries += s.out_ids.size();
         o->table2_bytes += (uint64_t)s.table2.size() * 4;
-        if (planned)
+        if (planned && plan.lean)
+            o->smem_states += std::min<uint64_t>(plan.mode == kLeanSmem32 ? s.states : s.rows_e16,
+                                                 plan.smem_rows);
+        else if (planned)
             o->smem_states += std::min<uint64_t>(plan.mode == 3 ? s.rows16 : s.states, plan.smem_rows);
     }
     o->build_ms = a->build_ms;
@@ -359,15 +377,18 @@ int ac_subset(const ac_automaton *a, uint32_t k, ac_subset_view *v) {
     v->table2 = s.table2.empty() ? nullptr : s.table2.data();
     v->table16 = s.table16.empty() ? nullptr : s.table16.data();
     v->rows16 = s.rows16;
+    v->table_e16 = s.table_e16.empty() ? nullptr : s.table_e16.data();
+    v->rows_e16 = s.rows_e16;
     return AC_OK;
 }
 
 int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
     if (!a || !cfg) return set_error(AC_EINVAL, "ac_set_scan_config: NULL argument");
-    if (cfg->threads && (cfg->threads % 32 || cfg->threads > 512))
-        return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 512");
+    if (cfg->threads && (cfg->threads % 32 || cfg->threads > 1024))
+        return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 1024");
     if (cfg->chains && cfg->chains != 1 && cfg->chains != 2 && cfg->chains != 4)
         return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
+    if (cfg->kernel > AC_KERNEL_LEAN) return set_error(AC_EINVAL, "ac_set_scan_config: unknown kernel %u", cfg->kernel);
     if (cfg->stage_bytes && cfg->stage_bytes != 16 && cfg->stage_bytes != 32)
         return set_error(AC_EINVAL, "ac_set_scan_config: stage bytes must be 16 or 32");
     if (cfg->stride > 2) return set_error(AC_EINVAL, "ac_set_scan_config: stride must be 0, 1 or 2");

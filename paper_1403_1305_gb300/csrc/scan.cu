@@ -6,6 +6,7 @@
 #include <cub/device/device_radix_sort.cuh>
 
 #include "scan_kernel.cuh"
+#include "scan_lean.cuh"
 
 namespace acgb {
 using namespace kern;
@@ -95,8 +96,11 @@ EncodeTiled encoder() {
     return fn;
 }
 
-// rows x row_bytes bytes at base, boxes of bx bytes x 32 rows
-int encode_rows_map(CUtensorMap *m, const uint8_t *base, uint64_t row_bytes, uint64_t rows, uint32_t bx) {
+// rows x row_bytes bytes at base, boxes of bx bytes x 32 rows. promote64:
+// L2 fills of 64 bytes instead of 256 (many rows in flight at once: the
+// promoted lines of every row must stay in L2 until their row reads them)
+int encode_rows_map(CUtensorMap *m, const uint8_t *base, uint64_t row_bytes, uint64_t rows, uint32_t bx,
+                    bool promote64 = false) {
     EncodeTiled enc = encoder();
     if (!enc) return set_error(AC_ECUDA, "scan: cuTensorMapEncodeTiled is not available");
     cuuint64_t dims[2] = {row_bytes, rows};
@@ -104,7 +108,8 @@ int encode_rows_map(CUtensorMap *m, const uint8_t *base, uint64_t row_bytes, uin
     cuuint32_t box[2] = {bx, 32};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)base, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     promote64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? AC_OK : set_error(AC_ECUDA, "scan: encoding the row tensor map failed (%d)", (int)r);
 }
@@ -137,8 +142,88 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg) {
     return 256 + 128 + 128 + warps * kNS * slot_bytes_for(cfg.chains, bx) + warps * kNS * 8;
 }
 
+// ------------------------------------------------------------------ lean kernel
+bool lean_shape_ok(uint32_t threads, uint32_t chains) {
+    return (threads == 1024 && (chains == 4 || chains == 2)) || (threads == 768 && chains == 4) ||
+           (threads == 512 && chains == 4);
+}
+
+// Why the lean kernel cannot scan format fmt of `a` under configuration c
+// (threads/chains 0 = its defaults), or nullptr when it can.
+const char *lean_unfit(const ac_automaton *a, const ac_scan_config &c, int fmt) {
+    if (a->machine != AC_MACHINE_DFA) return "it walks the folded machine only";
+    if (a->sigma != 4 || !(fmt == AC_PACKED2 || (fmt == AC_U8 && a->dna_acgt)))
+        return "it needs a 4-letter machine and ACGT bytes or packed text";
+    if (c.stride == 2) return "it uses the one-symbol table (stride 1)";
+    if (a->placement != AC_PLACE_AUTO && a->placement != AC_PLACE_SMEM && a->placement != AC_PLACE_HYBRID16)
+        return "it supports placements AUTO, SMEM and HYBRID16";
+    if (c.stage_bytes && c.stage_bytes != kern::kLeanBX) return "it uses 16-byte stages";
+    const uint32_t t = c.threads ? c.threads : 1024;
+    const uint32_t ch = c.chains ? c.chains : 4;
+    if (!lean_shape_ok(t, ch)) return "(threads, chains) must be (1024, 4), (1024, 2), (768, 4) or (512, 4)";
+    uint32_t max_states = 0;
+    for (auto &d : a->h_desc) {
+        if (d.states >= (1u << 28)) return "it needs fewer than 2^28 states per subset";
+        if (!d.table_e16) return "the escape-coded 16-bit prefix is missing";
+        max_states = std::max(max_states, d.states);
+    }
+    if (a->placement == AC_PLACE_SMEM) {
+        const int limit = scan_smem_limit(a->device);
+        uint64_t room = (uint64_t)std::max(0, limit - (int)kern::lean_stage_bytes(t, ch) - 128);
+        if (a->smem_cap_bytes && a->smem_cap_bytes < room) room = a->smem_cap_bytes;
+        if (c.smem_table_bytes && c.smem_table_bytes < room) room = c.smem_table_bytes;
+        if ((uint64_t)max_states * 16 > room) return "the whole table does not fit its shared memory";
+    }
+    return nullptr;
+}
+
+static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int fmt, ac_scan_config *cfg);
+
+// Would the general kernel's automatic plan use two symbols per lookup for
+// format fmt (the two-symbol table beats the lean one-symbol scan there)?
+static bool general_picks_stride2(const ac_automaton *a, int fmt) {
+    if (!a->has_table2 || scan_stride(a, fmt, 0) != 2) return false;
+    ac_scan_config base{}, g{};
+    base.kernel = AC_KERNEL_GENERAL;
+    fill_config(a, base, 1, fmt, &g);
+    ScanPlan plan{};
+    return plan_scan(a, g, fmt, &plan) == AC_OK && plan.stride == 2;
+}
+
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg) {
-    ac_scan_config c = a->cfg;
+    fill_config(a, a->cfg, n, fmt, cfg);
+}
+
+// The configuration a scan of n symbols (format fmt) runs with, from the
+// configuration c whose zero fields take their defaults.
+static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int fmt, ac_scan_config *cfg) {
+    const ac_scan_config given = c;
+    const bool lean_ok = c.kernel != AC_KERNEL_GENERAL && a->device >= 0 && !lean_unfit(a, c, fmt) &&
+                         !(c.kernel == AC_KERNEL_AUTO && c.stride == 0 && general_picks_stride2(a, fmt));
+    if (lean_ok) {
+        c.kernel = AC_KERNEL_LEAN;
+        if (!c.threads) c.threads = 1024;
+        if (!c.chains) c.chains = 4;
+        c.stage_bytes = kern::kLeanBX;
+        if (!c.row_len) {
+            int sms = 148;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device);
+            const uint64_t chains = (uint64_t)sms * c.threads * c.chains;
+            uint64_t want = (n + chains - 1) / chains;
+            // one machine: rows as short as twice the warm-up (at least one
+            // 32-byte block), so a short text still spreads over the SMs;
+            // subset machines: the general kernel's rule
+            const uint64_t block = fmt == AC_U8 ? 32 : 128;
+            const uint64_t lo = a->K == 1 ? std::max<uint64_t>(2 * block, 2ull * a->max_len)
+                                          : std::max<uint64_t>(256, 8ull * a->max_len);
+            uint64_t L = std::max<uint64_t>(want, lo);
+            if (L > (1u << 20)) L = 1u << 20;
+            c.row_len = (uint32_t)L;
+        }
+        *cfg = c;
+        return;
+    }
+    if (c.kernel == AC_KERNEL_AUTO) c.kernel = AC_KERNEL_GENERAL;
     if (!c.threads) c.threads = 512;
     if (!c.chains) c.chains = 2;
     // 16-byte stages leave more shared memory to the table and double the
@@ -153,13 +238,13 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
         for (auto &d : a->h_desc) biggest = std::max<uint64_t>(biggest, (uint64_t)d.states * a->sigma * 4);
         if (biggest > (160u << 10)) c.smem_table_bytes = 16u << 10;
     }
-    if (!a->cfg.chains && a->device >= 0 && a->machine == AC_MACHINE_DFA) {
+    if (!given.chains && a->device >= 0 && a->machine == AC_MACHINE_DFA) {
         // with the 16-bit prefix (a large 4-letter machine) most steps still
         // wait on L2 for some lane: 4 chains per thread keep more in flight
         ScanPlan plan{};
         if (plan_scan(a, c, fmt, &plan) == AC_OK && plan.mode == kern::MODE_H16) {
             c.chains = 4;
-            if (!a->cfg.stage_bytes) c.stage_bytes = 16;
+            if (!given.stage_bytes) c.stage_bytes = 16;
         }
     }
     if (!c.row_len) {
@@ -184,7 +269,43 @@ uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want) {
     return format_ok ? 2 : 1;
 }
 
+// Lean plan: every row in shared memory (32-bit row offsets) when the
+// largest subset fits, else the longest escape-coded 16-bit prefix that fits.
+static int plan_lean(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out) {
+    if (const char *why = lean_unfit(a, cfg, fmt)) return set_error(AC_EINVAL, "scan: lean kernel: %s", why);
+    const int limit = scan_smem_limit(a->device);
+    const uint32_t staging = kern::lean_stage_bytes(cfg.threads, cfg.chains);
+    if ((int)staging + 1024 > limit) return set_error(AC_EINVAL, "scan: lean staging does not fit in shared memory");
+    uint64_t avail = (uint64_t)limit - staging - 128;
+    if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
+    if (cfg.smem_table_bytes && cfg.smem_table_bytes < avail) avail = cfg.smem_table_bytes;
+    uint32_t max_states = 0, max_rows_e16 = 0;
+    for (auto &d : a->h_desc) {
+        max_states = std::max(max_states, d.states);
+        max_rows_e16 = std::max(max_rows_e16, d.rows_e16);
+    }
+    ScanPlan pl{};
+    pl.lean = true;
+    pl.stride = 1;
+    if ((uint64_t)max_states * 16 <= avail && a->placement != AC_PLACE_HYBRID16) {
+        pl.mode = kern::LEAN_SMEM32;
+        pl.smem_rows = max_states;
+        pl.table_words = max_states * 4;
+    } else {
+        if (a->placement == AC_PLACE_SMEM)
+            return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory", max_states);
+        pl.mode = kern::LEAN_E16;
+        pl.smem_rows = (uint32_t)std::min<uint64_t>(max_rows_e16, avail / 8);
+        pl.table_words = (pl.smem_rows * 2 + 3) & ~3u;
+    }
+    pl.smem = (((size_t)pl.table_words * 4 + 127) & ~(size_t)127) + staging;
+    if (pl.smem > (size_t)limit) return set_error(AC_EINVAL, "scan: lean shared memory plan exceeds the limit");
+    *out = pl;
+    return AC_OK;
+}
+
 int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out) {
+    if (cfg.kernel == AC_KERNEL_LEAN) return plan_lean(a, cfg, fmt, out);
     uint32_t max_states = 0, max_rows16 = 0;
     bool has16 = a->sigma == 4 && !a->h_desc.empty();
     for (auto &d : a->h_desc) {
@@ -349,9 +470,88 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
     return AC_OK;
 }
 
+// The lean kernel (scan_lean.cuh): one-symbol scan of ACGT bytes or packed text.
+static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
+                       cudaStream_t stream) {
+    const uint64_t nbytes = (t.fmt == AC_U8) ? t.n : (t.n + 3) / 4;
+    if (nbytes == 0) return AC_OK;
+    const uint64_t readable = std::max(nbytes, t.readable);
+    if (readable < kStageBytes) return set_error(AC_EINVAL, "scan: text buffer shorter than one stage");
+    if ((uintptr_t)t.d_text & 15) return set_error(AC_EINVAL, "scan: text must be 16-byte aligned");
+    ScanPlan plan{};
+    int rc = plan_lean(a, cfg, t.fmt, &plan);
+    if (rc) return rc;
+    const uint32_t sym_per_byte = (t.fmt == AC_U8) ? 1 : 4;
+    uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
+    rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
+    if (rb > (1u << 24)) rb = 1u << 24;
+    const uint64_t rmax = readable / kStageBytes * kStageBytes;
+    if (rb > rmax) rb = rmax;
+    if (rb == 0) rb = kStageBytes;
+
+    ScanParams p{};
+    p.text = t.d_text;
+    p.nbytes = nbytes;
+    p.nsym = t.n;
+    p.row_bytes = (uint32_t)rb;
+    p.full_rows = readable / rb;
+    const uint64_t covered = p.full_rows * rb;
+    p.tail_bytes = nbytes > covered ? (uint32_t)(nbytes - covered) : 0u;
+    p.num_rows = p.full_rows + (p.tail_bytes ? 1 : 0);
+    p.rows_per_tile = cfg.threads * cfg.chains;
+    p.K = a->K;
+    p.sigma = a->sigma;
+    p.subs = a->d_desc;
+    p.keys = o.keys;
+    p.cap = o.cap;
+    p.num = o.num;
+    p.counts = o.counts;
+    p.err = o.err;
+    p.key_shift = (uint32_t)key_shift_for(a);
+    p.smem_rows = plan.smem_rows;
+    p.table_words = plan.table_words;
+    memcpy(p.sym_of_byte, a->sym_of_byte, 256);
+    const uint64_t row_blocks = (p.num_rows + p.rows_per_tile - 1) / p.rows_per_tile;
+    p.num_tiles = row_blocks * a->K;
+    if (p.full_rows >= (1ull << 31) || p.num_rows * rb >= (1ull << 40))
+        return set_error(AC_ERANGE, "scan: text too long for the row tensor map");
+
+    CUtensorMap rows_map, tail_map;
+    memset(&rows_map, 0, sizeof(rows_map));
+    memset(&tail_map, 0, sizeof(tail_map));
+    rc = encode_rows_map(&rows_map, t.d_text, rb, p.full_rows, kern::kLeanBX, true);
+    if (rc) return rc;
+    if (p.tail_bytes) {
+        rc = encode_tail_map(&tail_map, t.d_text + covered, p.tail_bytes, kern::kLeanBX);
+        if (rc) return rc;
+    }
+    kern::LeanFn fn = nullptr;
+    if (t.fmt == AC_PACKED2)
+        fn = plan.mode == kern::LEAN_SMEM32 ? kern::lean_packed_smem32(cfg.threads, cfg.chains)
+                                            : kern::lean_packed_e16(cfg.threads, cfg.chains);
+    else
+        fn = plan.mode == kern::LEAN_SMEM32 ? kern::lean_u8_smem32(cfg.threads, cfg.chains)
+                                            : kern::lean_u8_e16(cfg.threads, cfg.chains);
+    if (!fn) return set_error(AC_EINVAL, "scan: no lean kernel for this configuration");
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device);
+    // one machine: warps take blocks of 32 * chains rows, so a CTA needs only
+    // one block; subset machines: CTA tiles of threads * chains rows
+    const uint64_t units = a->K == 1 ? (p.num_rows + 32ull * cfg.chains - 1) / (32ull * cfg.chains) : p.num_tiles;
+    uint64_t grid = cfg.ctas ? cfg.ctas : (uint64_t)sms;
+    if (grid > units) grid = units;
+    fn<<<(unsigned)grid, cfg.threads, plan.smem, stream>>>(p, rows_map, tail_map);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "scan launch: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg_in,
                 cudaStream_t stream) {
     if (a->machine == AC_MACHINE_PFAC) return launch_pfac(a, t, o, cfg_in, stream);
+    if (cfg_in.kernel == AC_KERNEL_LEAN) return launch_lean(a, t, o, cfg_in, stream);
     ac_scan_config cfg = cfg_in;
     if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)
         return set_error(AC_EINVAL, "scan: threads per CTA must be a multiple of 32 in [32, 512]");

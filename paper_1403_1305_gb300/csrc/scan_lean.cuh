@@ -1,0 +1,513 @@
+// The lean scan: one-symbol tables of a 4-letter machine over ACGT bytes or
+// 2-bit packed text, one text per launch.
+//
+// It computes exactly what scan_kernel computes (the folded AC-opt machine of
+// Section III walked one symbol at a time, Section II.A's output at every
+// flagged state; input-focused rows with a warm-up of longest pattern - 1
+// symbols, pattern-focused subsets as tiles), with a fast loop cut down to a
+// few instructions per symbol so that more chains fit on an SM:
+//
+//  * LEAN_SMEM32 (every row of the subset in shared memory): a shared-memory
+//    entry is the byte offset of the next state's row (next << 4) with the
+//    output bit in bit 0, so the next address is (entry & ~15) | 4*symbol --
+//    one logic instruction, one shared load, one OR into the stage's
+//    accumulator per symbol.
+//  * LEAN_E16 (larger machines): a breadth-first prefix of 16-bit entries in
+//    shared memory holding the next state itself, or an escape code when that
+//    state has an output or does not fit 16 bits; a lookup is one predicated
+//    shared load (state inside the prefix), then one predicated load of the
+//    32-bit table through L2 (state beyond the prefix, or an escape). The
+//    32-bit entry carries the output bit (bit 31), which the stage's OR
+//    accumulator collects.
+//
+// Text staging is the same tensor-map TMA pipeline as scan_kernel with one
+// slot per warp (the slot is refilled as soon as the lanes hold the stage in
+// registers, and a stage of lookups takes far longer than the copy), so the
+// staging costs 16 bytes of shared memory per chain. A stage whose
+// accumulator shows an output (or that holds a byte outside ACGT, or touches
+// a text edge) is walked again symbol by symbol by the whole warp
+// (lean_careful) and its matches are emitted through emit_warp.
+#pragma once
+
+#include "scan_kernel.cuh"
+
+namespace acgb {
+namespace kern {
+
+enum { LEAN_SMEM32 = kLeanSmem32, LEAN_E16 = kLeanE16 };
+constexpr uint32_t kLeanBX = 16;  // text bytes per chain per stage
+
+__host__ __device__ constexpr uint32_t lean_slot_bytes(uint32_t C) { return C * 32u * kLeanBX + 128u; }
+
+// shared memory of a lean CTA besides the table: byte map, one staging slot
+// and one mbarrier per warp, alignment
+__host__ __device__ constexpr uint32_t lean_stage_bytes(uint32_t threads, uint32_t C) {
+    return 256u + 128u + 128u + (threads / 32u) * (lean_slot_bytes(C) + 8u);
+}
+
+// E16 lookup of entry (state u, symbol): sa = its shared address in the 16-bit
+// prefix (read only when u < hot, i.e. u is a prefix row without the output
+// bit), gi = its byte offset there (the 32-bit table's byte offset is twice
+// that). An escape, or a state beyond the prefix, reads the 32-bit table.
+// Returns the next entry: a state id (16-bit prefix) or a 32-bit table entry
+// (state id | kFlag when its output is not empty).
+__device__ __forceinline__ uint32_t e16_step(uint32_t u, uint32_t sa, uint32_t gi, uint32_t hot,
+                                             const uint32_t *gtab) {
+    uint32_t e;
+    asm("{\n\t.reg .pred ps, pg;\n\t.reg .u64 ga;\n\t"
+        "setp.lt.u32 ps, %1, %3;\n\t"
+        "mov.u32 %0, 65535;\n\t"
+        "@ps ld.shared.u16 %0, [%2];\n\t"
+        "setp.eq.u32 pg, %0, 65535;\n\t"
+        "mad.wide.u32 ga, %4, 2, %5;\n\t"
+        "@pg ld.global.nc.L1::no_allocate.u32 %0, [ga];\n\t}"
+        : "=r"(e)
+        : "r"(u), "r"(sa), "r"(hot), "r"(gi), "l"(gtab));
+    return e;
+}
+
+// The text pipeline with 32-bit shared-window addresses (fewer registers than
+// generic pointers).
+__device__ __forceinline__ void mbar_expect_s(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_s(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false (and the error word set) after 2 s.
+__device__ __forceinline__ bool wait_phase_s(uint32_t bar, uint32_t parity, uint32_t *err) {
+    if (mbar_try_wait_s(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_s(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+            atomicOr(err, 1u);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_2d_s(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y, uint32_t bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_1d_s(uint32_t dst, const CUtensorMap *map, int32_t x, uint32_t bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2}], [%3], %4;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(bar), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+
+// Next state of clean state s on symbol c (< 4) in the 32-bit entry format
+// (next | kFlag when its output is not empty), for the careful walk.
+template <int LM>
+__device__ __forceinline__ uint32_t lean_lookup(const uint8_t *tab, uint32_t hot, const uint32_t *gtab,
+                                                uint32_t s, uint32_t c, uint64_t pol) {
+    if (LM == LEAN_SMEM32) {
+        const uint32_t e = reinterpret_cast<const uint32_t *>(tab)[s * 4u + c];
+        return (e >> 4) | (e << 31);
+    } else {
+        if (s < hot) {
+            const uint32_t e = reinterpret_cast<const uint16_t *>(tab)[s * 4u + c];
+            if (e != kEsc16) return e;
+        }
+        return ld_table(gtab + (size_t)s * 4u + c, pol);
+    }
+}
+
+// One stage of one chain walked symbol by symbol with every check (text
+// edges, bytes outside ACGT), emitting the output of every flagged state at
+// main-stage positions. The stage's 16 bytes (row `row`, byte offset o from
+// the row start; negative in the warm-up) are read again from global memory:
+// the staging slot has been refilled by then, and this path is rare. s_in is
+// a clean state id; returns the clean state after the stage. All 32 lanes
+// call it together. Inlined at a single site of the kernel (a call would make
+// the kernel keep its registers in local memory around it).
+template <int FMT, int LM>
+__device__ __forceinline__ uint32_t lean_careful(uint32_t s_in, uint64_t row, int64_t o, bool main_stage,
+                                             const ScanParams &p, const SubsetDev *sdp, const uint8_t *tab,
+                                             const uint8_t *smap, uint32_t hot, uint32_t lane) {
+    const SubsetDev &sd = *sdp;
+    const bool active = row < p.num_rows;
+    const int64_t b0 = (int64_t)row * (int64_t)p.row_bytes + o;  // byte offset of the stage in the text
+    uint32_t w[4] = {0, 0, 0, 0};
+    if (active) {
+        if (b0 >= 0 && b0 + 16 <= (int64_t)p.nbytes) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.text + b0));  // 16-byte aligned
+            w[0] = v.x;
+            w[1] = v.y;
+            w[2] = v.z;
+            w[3] = v.w;
+        } else {
+            for (int k = 0; k < 16; ++k)
+                if (b0 + k >= 0 && b0 + k < (int64_t)p.nbytes) w[k >> 2] |= (uint32_t)__ldg(p.text + b0 + k) << (8 * (k & 3));
+        }
+    }
+    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;
+    const int64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
+    const uint64_t pol = l2_evict_last();
+    const int64_t nsym = (int64_t)p.nsym;
+    uint32_t sc = s_in;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t wv = w[e];
+#pragma unroll 1
+        for (int b = 0; b < PER; ++b) {
+            const int64_t pos = pos0 + e * PER + b;
+            const bool live = active && pos >= 0 && pos < nsym;
+            bool has = false;
+            if (live) {
+                const uint32_t c = (FMT == FMT_U8) ? (uint32_t)smap[(wv >> (8 * b)) & 0xffu] : (wv >> (2 * b)) & 3u;
+                const uint32_t nv = c < 4u ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
+                sc = nv & kStateMask;
+                has = main_stage && (nv & kFlag);
+            } else if (pos < 0) {
+                sc = 0;
+            }
+            emit_warp(has, sc, (uint64_t)(pos < 0 ? 0 : pos), 0, sd, p, lane);
+        }
+    }
+    return sc;
+}
+
+// symbol code of 2-bit packed symbol b of word w, times 2 (E16) or 4 (SMEM32)
+template <int SH>
+__device__ __forceinline__ uint32_t packed_code(uint32_t w, int b) {
+    // code << SH = bits [2b, 2b+2) of w moved to [SH, SH+2)
+    return (2 * b >= SH ? (w >> (2 * b - SH)) : (w << (SH - 2 * b))) & (3u << SH);
+}
+
+template <int FMT, int LM, int C, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    lean_kernel(const __grid_constant__ ScanParams p, const __grid_constant__ CUtensorMap rows_map,
+                const __grid_constant__ CUtensorMap tail_map) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr uint32_t BX = kLeanBX;
+    constexpr uint32_t SYM = (FMT == FMT_U8) ? BX : BX * 4;  // symbols per stage
+    constexpr uint32_t SLOT = lean_slot_bytes(C);
+    constexpr uint32_t BOX = 32u * BX;
+    constexpr uint32_t FLAG = LM == LEAN_SMEM32 ? 1u : kFlag;
+
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint8_t *tab = smem;
+    uint8_t *smap = smem + (((size_t)p.table_words * 4 + 127) & ~(size_t)127);
+    uint8_t *stage = reinterpret_cast<uint8_t *>(((uintptr_t)(smap + 256) + 127) & ~(uintptr_t)127);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + (size_t)nwarps * SLOT);
+    const uint32_t my_stage = smem_addr(stage) + warp * SLOT;  // shared-window addresses
+    const uint32_t my_bar = smem_addr(bars + warp);
+
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < nwarps; ++i) mbar_init(bars + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    uint32_t parity = 0;
+    bool aborted = false;
+    const uint64_t xpol = l2_evict_first();  // text
+    const uint32_t sbase = smem_addr(tab);
+    const int64_t nsym = (int64_t)p.nsym;
+
+    // Stage subset k's table into shared memory (all threads of the CTA).
+    auto stage_table = [&](const SubsetDev *sdp, uint32_t hot) {
+        __syncthreads();  // every warp is done with the previous table
+        if (LM == LEAN_SMEM32) {
+            // entry -> (next << 4) | output bit: the byte offset of the next row
+            const uint32_t words = hot * 4u;
+            const uint32_t *gtab = sdp->table;
+            uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
+            for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+                const uint32_t e = __ldg(gtab + i);
+                t32[i] = ((e & kStateMask) << 4) | (e >> 31);
+            }
+        } else {
+            const uint32_t halves = hot * 4u;  // 16-bit entries
+            const uint4 *src4 = reinterpret_cast<const uint4 *>(sdp->table_e16);
+            uint4 *dst4 = reinterpret_cast<uint4 *>(tab);
+            for (uint32_t i = threadIdx.x; i < halves / 8; i += blockDim.x) dst4[i] = __ldg(src4 + i);
+            uint16_t *t16 = reinterpret_cast<uint16_t *>(tab);
+            for (uint32_t i = (halves & ~7u) + threadIdx.x; i < halves; i += blockDim.x)
+                t16[i] = __ldg(sdp->table_e16 + i);
+        }
+        __syncthreads();
+    };
+
+    // One warp scans rows [row0, row0 + 32*C) of the text with subset sdp.
+    auto run_rows = [&](const SubsetDev *sdp, uint32_t hot, uint64_t row0) {
+        const uint32_t *gtab = sdp->table;
+        const uint32_t warm = sdp->warm;
+        const uint32_t warm_bytes = (FMT == FMT_U8) ? warm : (warm + 3) / 4;
+        const uint32_t nW = (warm_bytes + BX - 1) / BX;
+        const uint32_t L32 = p.row_bytes;
+        const uint32_t nst = nW + L32 / BX;
+        // The partial last row of the text (if any) is read from global memory
+        // by the careful walk at every stage (its bytes beyond the text end are
+        // not in the row tensor map).
+        const bool tail_in_warp = p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
+        // Stages [s_lo, s_hi) have every row of the warp inside the text (no
+        // text edge, no partial row): their stages need no per-chain checks.
+        const uint64_t row_last = min(row0 + 32 * C, p.num_rows) - 1;
+        const uint64_t warm_total = (uint64_t)nW * BX;
+        const uint32_t s_lo = row0 * L32 >= warm_total ? 0u : (uint32_t)(nW - row0 * L32 / BX);
+        uint32_t s_hi = 0;
+        if (!tail_in_warp) {
+            const int64_t spb = (FMT == FMT_U8) ? 1 : 4;
+            const int64_t lim = ((int64_t)p.nsym - (int64_t)SYM) / spb - (int64_t)row_last * L32;  // max stage byte offset
+            if (p.nsym >= SYM && lim >= -(int64_t)warm_total) {
+                const int64_t last = (lim + (int64_t)warm_total) / BX + 1;
+                s_hi = last < (int64_t)nst ? (uint32_t)last : nst;
+            }
+        }
+        // tensor-map coordinates of stage 0 (x = byte column, dy = row delta),
+        // then advanced by BX per stage without a division
+        int32_t col, dy;
+        {
+            const uint32_t back = (uint32_t)warm_total;  // bytes before the row start
+            const uint32_t rows_back = (back + L32 - 1) / L32;
+            dy = -(int32_t)rows_back;
+            col = (int32_t)(rows_back * L32 - back);
+        }
+        uint32_t bytes = 0;
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (row0 + (uint64_t)j * 32 < p.full_rows) bytes += BOX;
+
+        // lane 0 issues one 2-D box per chain group that holds a full row
+        auto issue = [&]() {
+            mbar_expect_s(my_bar, bytes);
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (row0 + (uint64_t)j * 32 < p.full_rows)
+                    tma_2d_s(my_stage + j * BOX, &rows_map, col, (int32_t)(row0 + j * 32) + dy, my_bar, xpol);
+        };
+        auto advance = [&]() {
+            col += BX;
+            if (col >= (int32_t)L32) {
+                col -= (int32_t)L32;
+                dy += 1;
+            }
+        };
+        // a warp whose rows are all beyond the full rows (only the partial last
+        // row) has nothing to copy: its stages are all walked carefully
+        const bool copies = bytes != 0;
+        if (copies && lane == 0) issue();
+        advance();
+        const uint32_t rd = my_stage + lane * BX;  // this lane's row in each chain group's box
+
+        uint32_t st[C];  // state per chain: SMEM32 row offset (| output bit), E16 id (| kFlag)
+#pragma unroll
+        for (int j = 0; j < C; ++j) st[j] = 0;
+
+        for (uint32_t s = 0; s < nst; ++s) {
+            if (copies) {
+                if (!wait_phase_s(my_bar, parity & 1u, p.err)) {
+                    aborted = true;
+                    return;
+                }
+                parity ^= 1u;
+            }
+            const bool main_stage = s >= nW;
+            uint32_t u[C], acc[C], bad = 0;  // bad: bytes outside ACGT in any chain of the thread
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                u[j] = st[j];
+                acc[j] = 0;
+            }
+            // The stage is read from the slot in two 8-byte halves; the slot is
+            // refilled once the second half is in registers. The C chains
+            // advance together, one lookup each per round, so their lookups are
+            // independent and overlap. Chains off the fast path walk in-bounds
+            // garbage that is discarded.
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint2 half[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) half[j] = lds64(rd + j * BOX + 8 * h);
+                if (h == 1) {
+                    __syncwarp();
+                    if (s + 1 < nst) {
+                        fence_proxy_async();
+                        if (copies && lane == 0) issue();
+                        advance();
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    uint32_t cw[C];
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        const uint32_t w = e == 0 ? half[j].x : half[j].y;
+                        if (FMT == FMT_U8) {
+                            // ACGT -> code k in bits [SH, SH+2) of each byte (SH = 2 or 1)
+                            cw[j] = LM == LEAN_SMEM32 ? ((w ^ (w << 1)) & 0x0c0c0c0cu) : ((w ^ (w >> 1)) & 0x06060606u);
+                            bad |= acgt_mismatch4(w, LM == LEAN_SMEM32 ? cw[j] >> 2 : cw[j] >> 1);
+                        } else {
+                            cw[j] = w;
+                        }
+                    }
+                    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;
+                    uint32_t prev[C];  // the previous step's entry, ORed in with the current one
+#pragma unroll
+                    for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            if (LM == LEAN_SMEM32) {
+                                const uint32_t c4 =
+                                    (FMT == FMT_U8) ? __byte_perm(cw[j], 0, 0x4440 + b) : packed_code<2>(cw[j], b);
+                                u[j] = *reinterpret_cast<const uint32_t *>(tab + ((u[j] & ~15u) | c4));
+                            } else {
+                                const uint32_t c2 =
+                                    (FMT == FMT_U8) ? __byte_perm(cw[j], 0, 0x4440 + b) : packed_code<1>(cw[j], b);
+                                const uint32_t gi = (u[j] << 3) + c2;
+                                u[j] = e16_step(u[j], sbase + gi, gi, hot, gtab);
+                            }
+                            if (b & 1) acc[j] |= prev[j] | u[j];
+                            else prev[j] = u[j];
+                        }
+                    }
+                }
+            }
+            // Common case: every chain of the warp inside the text and one vote
+            // finds no lane with an output or a byte outside ACGT.
+            bool slow = true;
+            if (s >= s_lo && s < s_hi) {
+                uint32_t flags = bad;
+                if (main_stage) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) flags |= acc[j] & FLAG;
+                }
+                slow = __any_sync(kFull, flags != 0);
+            }
+            if (!slow) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) st[j] = u[j];
+            } else {
+                // chain by chain (a rolled loop over a rotation of the per-chain
+                // registers, so the careful walk is inlined once): positions,
+                // then a careful walk wherever a lane of the chain needs one
+                const int64_t o = ((int64_t)s - (int64_t)nW) * BX;
+#pragma unroll 1
+                for (uint32_t jj = 0; jj < (uint32_t)C; ++jj) {
+                    const uint64_t row = row0 + (uint64_t)jj * 32 + lane;
+                    const int64_t b0 = (int64_t)row * L32 + o;
+                    const int64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
+                    const bool dead = row >= p.num_rows || pos0 >= nsym;
+                    const bool before = !dead && pos0 + (int64_t)SYM <= 0;
+                    const bool fast = !dead && pos0 >= 0 && pos0 + (int64_t)SYM <= nsym && row < p.full_rows;
+                    const bool need = !dead && !before && (!fast || bad != 0 || (main_stage && (acc[0] & FLAG)));
+                    uint32_t nx = u[0];
+                    if (__any_sync(kFull, need)) {
+                        const uint32_t s_in = LM == LEAN_SMEM32 ? (st[0] >> 4) : (st[0] & kStateMask);
+                        const uint32_t sc = lean_careful<FMT, LM>(s_in, row, o, main_stage, p, sdp, tab, smap, hot, lane);
+                        if (need) nx = LM == LEAN_SMEM32 ? (sc << 4) : sc;
+                    }
+                    nx = before ? 0u : nx;
+                    // rotate: chain jj + 1 moves to index 0, chain jj's new state to index C - 1
+#pragma unroll
+                    for (int j = 0; j + 1 < C; ++j) {
+                        u[j] = u[j + 1];
+                        acc[j] = acc[j + 1];
+                        st[j] = st[j + 1];
+                    }
+                    st[C - 1] = nx;
+                }
+            }
+        }
+    };
+
+    auto hot_of = [&](const SubsetDev *sdp) -> uint32_t {
+        return LM == LEAN_SMEM32 ? sdp->states : min(sdp->rows_e16, p.smem_rows);
+    };
+
+    if (p.K == 1) {
+        // one machine: the table is staged once and each warp takes its own
+        // blocks of 32*C rows, spread over the CTAs first (a short text still
+        // reaches many SMs)
+        const SubsetDev *sdp = p.subs;
+        const uint32_t hot = hot_of(sdp);
+        stage_table(sdp, hot);
+        const uint64_t blocks = (p.num_rows + 32 * C - 1) / (32 * C);
+        for (uint64_t t = (uint64_t)warp * gridDim.x + blockIdx.x; t < blocks && !aborted;
+             t += (uint64_t)gridDim.x * nwarps)
+            run_rows(sdp, hot, t * 32 * C);
+    } else {
+        // subset machines: tiles of (threads * C rows, subset), subset index
+        // fastest so concurrent CTAs share text rows in L2; the table is staged
+        // again when a CTA's subset changes
+        int cur_k = -1;
+        for (uint64_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+            const uint32_t k = (uint32_t)(tile % p.K);
+            const SubsetDev *sdp = p.subs + k;
+            const uint32_t hot = hot_of(sdp);
+            if ((int)k != cur_k) {
+                stage_table(sdp, hot);
+                cur_k = (int)k;
+            }
+            if (aborted) continue;  // keeps taking part in the CTA barriers, does no work
+            const uint64_t row0 = (tile / p.K) * p.rows_per_tile + (uint64_t)warp * 32 * C;
+            if (row0 < p.num_rows) run_rows(sdp, hot, row0);
+        }
+    }
+    if (aborted && lane == 0) {
+        // let a copy already issued by this warp land before the CTA exits (bounded)
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait_s(my_bar, parity & 1u) && global_ns() - t0 < 100000000ull) {
+        }
+    }
+}
+
+using LeanFn = void (*)(ScanParams, CUtensorMap, CUtensorMap);
+
+// lean shapes: (threads, chains) in {(1024, 4), (1024, 2), (768, 4), (512, 4)}
+template <int FMT, int LM>
+LeanFn pick_lean_shape(uint32_t threads, uint32_t C) {
+    if (threads == 1024) {
+        if (C == 4) return lean_kernel<FMT, LM, 4, 1024>;
+        if (C == 2) return lean_kernel<FMT, LM, 2, 1024>;
+    } else if (threads == 768 && C == 4) {
+        return lean_kernel<FMT, LM, 4, 768>;
+    } else if (threads == 512 && C == 4) {
+        return lean_kernel<FMT, LM, 4, 512>;
+    }
+    return nullptr;
+}
+
+// defined in the scan_lean_*.cu translation units
+LeanFn lean_u8_smem32(uint32_t threads, uint32_t C);
+LeanFn lean_u8_e16(uint32_t threads, uint32_t C);
+LeanFn lean_packed_smem32(uint32_t threads, uint32_t C);
+LeanFn lean_packed_e16(uint32_t threads, uint32_t C);
+
+}  // namespace kern
+}  // namespace acgb

@@ -49,23 +49,35 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
         }
         return best_ms;
     };
-    // 1. CTA shape (threads x chains x stage bytes) at the default row length and table
+    // 1. kernel and CTA shape (threads x chains x stage bytes) at the default
+    // row length and table
     ac_scan_config best{};
     float best_ms = 1e30f;
+    auto try_shape = [&](uint32_t kernel, uint32_t t, uint32_t ch, uint32_t stage) {
+        a->cfg = ac_scan_config{};
+        a->cfg.threads = t;
+        a->cfg.chains = ch;
+        a->cfg.stage_bytes = stage;
+        a->cfg.kernel = kernel;
+        ac_scan_config c;
+        default_config(a, n, fmt, &c);
+        const float ms = timeit(c);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
     const uint32_t threads[2] = {256, 512}, chains[3] = {1, 2, 4}, stages[2] = {16, 32};
     for (int ti = 0; ti < 2 && rc == AC_OK; ++ti)
         for (int ci = 0; ci < 3 && rc == AC_OK; ++ci)
             for (int si = 0; si < 2 && rc == AC_OK; ++si) {
                 if (stages[si] == 16 && chains[ci] == 1) continue;
-                a->cfg = ac_scan_config{0, threads[ti], chains[ci], 0, stages[si], 0};
-                ac_scan_config c;
-                default_config(a, n, fmt, &c);
-                const float ms = timeit(c);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
-                }
+                try_shape(AC_KERNEL_GENERAL, threads[ti], chains[ci], stages[si]);
             }
+    // the lean kernel where it applies (its shapes; a candidate that does not apply times as 1e30)
+    const uint32_t lean_shapes[4][2] = {{1024, 4}, {1024, 2}, {768, 4}, {512, 4}};
+    for (int li = 0; li < 4 && rc == AC_OK; ++li)
+        try_shape(AC_KERNEL_LEAN, lean_shapes[li][0], lean_shapes[li][1], 16);
     // 2. shared-memory table size (the rest goes through L1/L2)
     const uint32_t caps[5] = {0, 96u << 10, 48u << 10, 16u << 10, 4u << 10};
     ac_scan_config base = best;
@@ -85,6 +97,13 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
         for (uint32_t stride = 1; stride <= 2 && rc == AC_OK; ++stride) {
             ac_scan_config c = base;
             c.stride = stride;
+            if (stride == 2 && c.kernel == AC_KERNEL_LEAN) {
+                // two symbols per lookup run on the general kernel with its default shape
+                a->cfg = ac_scan_config{};
+                a->cfg.stride = 2;
+                a->cfg.kernel = AC_KERNEL_GENERAL;
+                default_config(a, n, fmt, &c);
+            }
             const float ms = timeit(c);
             if (ms < best_ms) {
                 best_ms = ms;

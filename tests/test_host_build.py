@@ -279,3 +279,51 @@ def test_sixteen_bit_prefix():
     assert A.ac_subset(A.ac_build([b"ab", b"ba"], device=-1), 0)["table16"] is None
     small = A.ac_subset(A.ac_build([b"ACGT", b"GA"], alphabet="ACGT", device=-1), 0)
     assert small["table16"].shape[0] == small["states"]
+
+
+def walk_e16(v, text, hot):
+    """Scan with the escape-coded 16-bit prefix as the lean kernel reads it:
+    a state below `hot` reads its 16-bit entry, an escape (or a state at or
+    beyond `hot`) reads the 32-bit table, whose entry carries the output bit."""
+    T, E, off, ids, sym = v["table"], v["table_e16"], v["out_off"], v["out_ids"], v["symbol_of_byte"]
+    res, s = [], 0
+    for i, b in enumerate(np.asarray(text, dtype=np.uint8).tolist()):
+        c = int(sym[b])
+        if c >= 4:
+            s = 0
+            continue
+        e = int(E[s, c]) if s < hot else 0xFFFF
+        if e == 0xFFFF:
+            e = int(T[s, c])
+        s = e & 0x7FFFFFFF
+        if e >> 31:
+            res += [(i, int(j)) for j in ids[off[s]:off[s + 1]]]
+    res.sort()
+    return np.asarray(res, dtype=np.uint32).reshape(-1, 2)
+
+
+def test_escape_coded_prefix():
+    """The lean kernel's shared-memory table: rows [0, min(states, 32768)),
+    entry = next state when it is below 65,535 and has an empty output, else
+    the escape 65,535. A machine wide enough that prefix rows lead to states
+    beyond 65,535 (100,000 patterns) has both kinds of escape; walking it with
+    prefixes of several lengths gives the oracle's matches."""
+    rng = np.random.default_rng(1600)
+    text = workloads.dna_text(rng, 60_000)
+    pats = workloads.draw_patterns(rng, text, 100_000, 12, 20, 0.5, np.frombuffer(b"ACGT", np.uint8))
+    pats += [b"ACG", b"TTAG", b"GATTA"]   # outputs at shallow states
+    a = A.ac_build(pats, alphabet="ACGT", device=-1)
+    v = A.ac_subset(a, 0)
+    T, E = v["table"], v["table_e16"]
+    r = E.shape[0]
+    assert r == min(v["states"], 1 << 15) and v["states"] > 1 << 16
+    nxt, flag = T[:r] & 0x7FFFFFFF, T[:r] >> 31
+    want_e = np.where((nxt < 0xFFFF) & (flag == 0), nxt, 0xFFFF)
+    assert np.array_equal(E.astype(np.uint32), want_e)
+    assert ((nxt >= 0xFFFF) & (E == 0xFFFF)).any() and ((flag == 1) & (E == 0xFFFF)).any()
+    want = oracle.scan(pats, text)[0]
+    for hot in (0, 5, 1000, r):
+        assert np.array_equal(walk_e16(v, text[:20_000] if hot < r else text, hot),
+                              oracle.scan(pats, text[:20_000] if hot < r else text)[0])
+    assert want.shape[0] > 0
+    assert A.ac_subset(A.ac_build([b"ab", b"ba"], device=-1), 0)["table_e16"] is None
