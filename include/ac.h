@@ -117,7 +117,16 @@ typedef struct {
                                   only, else AC_EINVAL). The two-symbol table composes two transitions of the
                                   one-symbol table (16 columns per state, 4x its memory) so a scan does one
                                   dependent lookup per two text symbols; results are the same. */
+    uint32_t builder;          /* AC_BUILDER_HOST (default) or AC_BUILDER_DEVICE: where the goto, failure and
+                                  output functions are constructed; the machine is the same, state for state */
 } ac_build_opts;
+
+/* Machine construction (ac_build_opts.builder). */
+#define AC_BUILDER_HOST 0   /* host threads, one per subset */
+#define AC_BUILDER_DEVICE 1 /* on the automaton's GPU (DFA machine, device >= 0; else AC_EINVAL): patterns
+                               sorted by symbol string, the trie numbered breadth-first from the longest
+                               common prefixes of neighbours in that order, failure function, fold and output
+                               function one depth at a time; the tables are then copied to the host view */
 
 typedef struct {
     ac_match *matches;     /* host array of num_matches records, sorted; library-owned */

@@ -28,6 +28,7 @@ AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL, AC_PLACE_OPT, AC
 AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
 AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
 AC_KERNEL_AUTO, AC_KERNEL_GENERAL, AC_KERNEL_LEAN = 0, 1, 2
+AC_BUILDER_HOST, AC_BUILDER_DEVICE = 0, 1
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
@@ -51,7 +52,7 @@ class ac_match(C.Structure):
 class ac_build_opts(C.Structure):
     _fields_ = [("alphabet", C.c_char_p), ("num_subsets", C.c_uint32), ("placement", C.c_int32),
                 ("device", C.c_int32), ("smem_table_bytes", C.c_uint32), ("machine", C.c_int32),
-                ("stride", C.c_uint32)]
+                ("stride", C.c_uint32), ("builder", C.c_uint32)]
 
 
 class ac_result(C.Structure):
@@ -242,7 +243,7 @@ class Automaton:
 
 def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_PLACE_AUTO,
              device: int = 0, smem_table_bytes: int = 0, machine: int = AC_MACHINE_DFA,
-             stride: int = 0) -> Automaton:
+             stride: int = 0, builder: int = AC_BUILDER_HOST) -> Automaton:
     pats = [p.encode() if isinstance(p, str) else bytes(p) for p in patterns]
     # one contiguous buffer; pattern j starts at offs[j] (empty patterns get a NULL pointer)
     blob = np.frombuffer(b"".join(pats) or b"\0", dtype=np.uint8)
@@ -256,7 +257,7 @@ def ac_build(patterns, alphabet=None, num_subsets: int = 1, placement: int = AC_
     lens = lens_np.ctypes.data_as(C.POINTER(C.c_uint32)) if len(pats) else (C.c_uint32 * 1)()
     if isinstance(alphabet, str):
         alphabet = alphabet.encode()
-    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine, stride)
+    opts = ac_build_opts(alphabet, num_subsets, placement, device, smem_table_bytes, machine, stride, builder)
     h = C.c_void_p()
     _check(lib().ac_build(ptrs, lens, len(pats), C.byref(opts), C.byref(h)), "ac_build")
     del blob, addr, lens_np  # the library copied what it needs

@@ -113,6 +113,9 @@ namespace acgb {
 // build.cpp
 int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
                    ac_automaton *a);
+// gbuild.cu: subset [lo, hi) built on the current device (same machine as the host build)
+int build_subset_device(const uint8_t *const *pats, const uint32_t *lens, uint32_t lo, uint32_t hi,
+                        const uint8_t *sym_of_byte, uint32_t sigma, HostSubset &S, std::string &why);
 // symbols per lookup a scan of this format uses under configuration stride `want` (0 = automatic)
 uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want);
 
@@ -197,11 +200,13 @@ int launch_pad_keys(unsigned long long *keys, const unsigned long long *num, uin
 int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t stream);
 // single-launch pad + sort + record conversion for at most kSmallSortMax keys
 constexpr uint64_t kSmallSortMax = 8192;
-int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int end_bit,
-                      uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
+                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
                       cudaStream_t stream);
-int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int end_bit,
+int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int begin_bit, int end_bit,
               void *temp, size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted);
+// first key bit a sort of a's keys must look at (stable sorts)
+int sort_begin_bit(const ac_automaton *a);
 
 // memory (capi.cu)
 void *dev_alloc(size_t bytes, cudaStream_t stream);

@@ -335,7 +335,7 @@ int device_sequence(Plan &P, cudaStream_t s) {
     const int end_bit = (int)std::min<uint32_t>(64, P.key_shift + value_bits(P.rows * P.row_bytes * 4));
     unsigned long long *sorted = nullptr;
     size_t tb = P.sort_bytes;
-    rc = sort_keys(P.d_keys, P.d_alt, P.cap, end_bit, P.d_sort, &tb, s, &sorted);
+    rc = sort_keys(P.d_keys, P.d_alt, P.cap, 0, end_bit, P.d_sort, &tb, s, &sorted);
     if (rc) return rc;
     const uint32_t ni = (uint32_t)P.items.size();
     uint64_t blocks = std::min<uint64_t>(2048, (P.cap + 255) / 256);

@@ -382,6 +382,29 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
     a->subs.assign(K, HostSubset());
     std::vector<int> rc(K, AC_OK);
     std::vector<std::string> why(K);
+    const uint32_t builder = opts ? opts->builder : AC_BUILDER_HOST;
+    if (builder > AC_BUILDER_DEVICE) return set_error(AC_EINVAL, "ac_build: unknown builder %u", builder);
+    if (builder == AC_BUILDER_DEVICE && (a->machine != AC_MACHINE_DFA || a->device < 0))
+        return set_error(AC_EINVAL, "ac_build: the device builder needs the DFA machine and a device");
+    if (builder == AC_BUILDER_DEVICE) {
+        // on the GPU, one subset after another; then the same derived tables
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (cudaSetDevice(a->device) != cudaSuccess) return set_error(AC_ECUDA, "ac_build: cannot use device %d", a->device);
+        for (uint32_t k = 0; k < K; ++k) {
+            const uint32_t lo = (uint32_t)((uint64_t)k * P / K), hi = (uint32_t)((uint64_t)(k + 1) * P / K);
+            try {
+                rc[k] = build_subset_device(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
+            } catch (const std::bad_alloc &) {
+                rc[k] = AC_ENOMEM;
+                why[k] = "host allocation failed";
+            }
+            if (rc[k] != AC_OK) break;
+        }
+        if (prev >= 0 && prev != a->device) cudaSetDevice(prev);
+        for (uint32_t k = 0; k < K; ++k)
+            if (rc[k] != AC_OK) return set_error(rc[k], "ac_build: subset %u on the device: %s", k, why[k].c_str());
+    }
     unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     unsigned nthr = std::min<unsigned>(K, hw);
     std::atomic<uint32_t> next{0};
@@ -391,9 +414,11 @@ int build_machines(const uint8_t *const *pats, const uint32_t *lens, uint32_t P,
             if (k >= K) break;
             uint32_t lo = (uint32_t)((uint64_t)k * P / K), hi = (uint32_t)((uint64_t)(k + 1) * P / K);
             try {
-                rc[k] = a->machine == AC_MACHINE_PFAC
-                            ? build_subset_pfac(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k])
-                            : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
+                // (the device builder has built the subsets already; the derived tables follow here)
+                if (builder != AC_BUILDER_DEVICE)
+                    rc[k] = a->machine == AC_MACHINE_PFAC
+                                ? build_subset_pfac(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k])
+                                : build_subset(pats, lens, lo, hi, a->sym_of_byte, sigma, a->subs[k], why[k]);
                 if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA) build_tail_mass(a->subs[k], sigma, prob);
                 if (rc[k] == AC_OK && a->machine == AC_MACHINE_DFA && sigma == 4) {
                     build_table16(a->subs[k]);

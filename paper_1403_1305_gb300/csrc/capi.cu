@@ -472,7 +472,7 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             ac_match *d_m = (ac_match *)sc.get(M * sizeof(ac_match));
             if (!d_m) return set_error(AC_ENOMEM, "ac_scan: records");
             const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
-            e = launch_small_sort(keys, num, M, end_bit, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
+            e = launch_small_sort(keys, num, M, sort_begin_bit(a), end_bit, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
             if (e) return e;
             r.matches = (ac_match *)malloc(M * sizeof(ac_match));
             if (!r.matches) return set_error(AC_ENOMEM, "ac_scan: host matches");
@@ -483,12 +483,12 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             if (!alt) return set_error(AC_ENOMEM, "ac_scan: sort buffer");
             const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
             size_t tb = 0;
-            e = sort_keys(keys, alt, M, end_bit, nullptr, &tb, s, nullptr);
+            e = sort_keys(keys, alt, M, sort_begin_bit(a), end_bit, nullptr, &tb, s, nullptr);
             if (e) return e;
             void *temp = sc.get(tb);
             if (!temp) return set_error(AC_ENOMEM, "ac_scan: sort scratch");
             unsigned long long *sorted = nullptr;
-            e = sort_keys(keys, alt, M, end_bit, temp, &tb, s, &sorted);
+            e = sort_keys(keys, alt, M, sort_begin_bit(a), end_bit, temp, &tb, s, &sorted);
             if (e) return e;
             ac_match *d_m = (ac_match *)(sorted == keys ? (void *)alt : (void *)keys);
             e = launch_keys_to_matches(sorted, num, M, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
@@ -555,7 +555,8 @@ int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, cons
     cudaStream_t s = (cudaStream_t)stream;
     if (cap <= kSmallSortMax) {
         const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n ? n - 1 : 0));
-        return launch_small_sort((const unsigned long long *)d_keys, (const unsigned long long *)d_num, cap, end_bit,
+        return launch_small_sort((const unsigned long long *)d_keys, (const unsigned long long *)d_num, cap,
+                                 sort_begin_bit(a), end_bit,
                                  (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, nullptr, s);
     }
     Scratch sc(s);
@@ -570,11 +571,11 @@ int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, cons
         if (rc) return rc;
         const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n ? n - 1 : 0));
         size_t tb = 0;
-        rc = sort_keys((unsigned long long *)d_keys, alt, cap, end_bit, nullptr, &tb, s, nullptr);
+        rc = sort_keys((unsigned long long *)d_keys, alt, cap, sort_begin_bit(a), end_bit, nullptr, &tb, s, nullptr);
         if (rc) return rc;
         void *temp = sc.get(tb);
         if (!temp) return set_error(AC_ENOMEM, "ac_sort_keys_async: sort scratch");
-        rc = sort_keys((unsigned long long *)d_keys, alt, cap, end_bit, temp, &tb, s, &sorted);
+        rc = sort_keys((unsigned long long *)d_keys, alt, cap, sort_begin_bit(a), end_bit, temp, &tb, s, &sorted);
         if (rc) return rc;
     }
     return launch_keys_to_matches(sorted, (const unsigned long long *)d_num, cap, (uint32_t)key_shift_for(a),

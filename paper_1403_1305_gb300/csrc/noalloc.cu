@@ -148,12 +148,12 @@ extern "C" int ac_scan_noalloc(const ac_automaton *a, const uint8_t *d_text, uin
         if (rc) return rc;
         const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + value_bits(n ? n - 1 : 0));
         size_t need = 0;
-        rc = sort_keys(keys, alt, kcap, end_bit, nullptr, &need, s, nullptr);
+        rc = sort_keys(keys, alt, kcap, sort_begin_bit(a), end_bit, nullptr, &need, s, nullptr);
         if (rc) return rc;
         if (need > kNoAllocSortBytes)
             return set_error(AC_ERANGE, "ac_scan_noalloc: sort storage %zu bytes beyond the fixed limit", need);
         size_t have = kNoAllocSortBytes;
-        rc = sort_keys(keys, alt, kcap, end_bit, sort_tmp, &have, s, &sorted);
+        rc = sort_keys(keys, alt, kcap, sort_begin_bit(a), end_bit, sort_tmp, &have, s, &sorted);
         if (rc) return rc;
     }
     return launch_keys_to_matches(sorted, num, cap, (uint32_t)key_shift_for(a), d_matches,

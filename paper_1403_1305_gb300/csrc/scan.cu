@@ -388,6 +388,15 @@ int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPla
 
 int key_shift_for(const ac_automaton *a) { return (int)bits_for(a->P ? a->P - 1 : 0); }
 
+// One folded machine: every match at a position is emitted by the one chain
+// that owns the position, as its state's output (ids ascending) into
+// consecutive slots, so a stable sort by the position bits alone orders the
+// keys. Subsets and the failure-less machine emit a position's matches from
+// several chains: the whole key is sorted.
+int sort_begin_bit(const ac_automaton *a) {
+    return (a->machine == AC_MACHINE_DFA && a->K == 1) ? key_shift_for(a) : 0;
+}
+
 int plan_smem(int device, const ac_scan_config &cfg, uint32_t sigma, int placement, uint32_t smem_cap,
               uint32_t max_states, uint32_t *rows_used, bool *hybrid, size_t *smem_bytes, uint32_t *table_words) {
     // shared memory: table prefix (rounded to 128 bytes) + map + staging + barriers
@@ -675,28 +684,30 @@ int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t
 // rest as all-ones), radix-sorts them in shared memory and writes the
 // (position, id) records -- pad, sort and conversion in one launch.
 namespace {
-constexpr int kSmallThreads = 1024, kSmallItems = 8;
-using SmallSort = cub::BlockRadixSort<unsigned long long, kSmallThreads, kSmallItems>;
+// 6-bit digits: the rank counters (64 digits x 1024 threads) still fit in shared memory
+template <int T, int I>
+using SmallSort = cub::BlockRadixSort<unsigned long long, T, I, cub::NullType, 6>;
 
-__global__ void __launch_bounds__(kSmallThreads, 1)
+template <int T, int I>
+__global__ void __launch_bounds__(T, 1)
     small_sort_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num, uint64_t cap,
-                      int end_bit, uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out,
+                      int begin_bit, int end_bit, uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out,
                       const uint32_t *err) {
     extern __shared__ __align__(16) unsigned char tmp[];
-    typename SmallSort::TempStorage &ts = *reinterpret_cast<typename SmallSort::TempStorage *>(tmp);
+    typename SmallSort<T, I>::TempStorage &ts = *reinterpret_cast<typename SmallSort<T, I>::TempStorage *>(tmp);
     const unsigned long long M = *num;
     const uint64_t m = M < cap ? M : cap;
-    unsigned long long k[kSmallItems];
+    unsigned long long k[I];
 #pragma unroll
-    for (int i = 0; i < kSmallItems; ++i) {
-        const uint64_t idx = (uint64_t)threadIdx.x * kSmallItems + i;
+    for (int i = 0; i < I; ++i) {
+        const uint64_t idx = (uint64_t)threadIdx.x * I + i;
         k[i] = idx < m ? keys[idx] : ~0ull;
     }
-    SmallSort(ts).Sort(k, 0, end_bit);
+    SmallSort<T, I>(ts).Sort(k, begin_bit, end_bit);
     const unsigned long long mask = (1ull << shift) - 1ull;
 #pragma unroll
-    for (int i = 0; i < kSmallItems; ++i) {
-        const uint64_t idx = (uint64_t)threadIdx.x * kSmallItems + i;
+    for (int i = 0; i < I; ++i) {
+        const uint64_t idx = (uint64_t)threadIdx.x * I + i;
         if (idx < m) {
             ac_match r;
             r.pos = (uint32_t)(k[i] >> shift);
@@ -706,30 +717,42 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     }
     if (threadIdx.x == 0 && num_out) *num_out = (err && *err) ? ~0ull : M;
 }
-}  // namespace
 
-int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int end_bit,
-                      uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
+// one CTA sized to the capacity (the sort's passes cost in proportion to the items)
+template <int T, int I>
+int small_sort_launch(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
+                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
                       cudaStream_t stream) {
-    if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
-                                              (unsigned long long)kSmallSortMax);
-    const int smem = (int)sizeof(typename SmallSort::TempStorage);
+    const int smem = (int)sizeof(typename SmallSort<T, I>::TempStorage);
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(small_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = cudaFuncSetAttribute(small_sort_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     if (attr != cudaSuccess) return set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(attr));
-    small_sort_kernel<<<1, kSmallThreads, smem, stream>>>(keys, num, cap, end_bit, shift, out, num_out, err);
+    small_sort_kernel<T, I><<<1, T, smem, stream>>>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(e));
 }
+}  // namespace
 
-int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int end_bit, void *temp,
-              size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted) {
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
+                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
+                      cudaStream_t stream) {
+    if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
+                                              (unsigned long long)kSmallSortMax);
+    if (cap <= 512)
+        return small_sort_launch<128, 4>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
+    if (cap <= 2048)
+        return small_sort_launch<256, 8>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
+    return small_sort_launch<1024, 8>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
+}
+
+int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int begin_bit, int end_bit,
+              void *temp, size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted) {
     if (count > 0x7fffffffull) return set_error(AC_ERANGE, "sort: too many matches");
     cub::DoubleBuffer<unsigned long long> db(keys, keys_alt);
-    cudaError_t e = cub::DeviceRadixSort::SortKeys(temp, *temp_bytes, db, (int)count, 0, end_bit, stream);
+    cudaError_t e = cub::DeviceRadixSort::SortKeys(temp, *temp_bytes, db, (int)count, begin_bit, end_bit, stream);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "sort: %s", cudaGetErrorString(e));
     if (sorted) *sorted = db.Current();
     return AC_OK;

@@ -140,6 +140,16 @@ def test_argument_errors():
         A.ac_set_scan_config(a, threads=48)
     with pytest.raises(A.AcError):
         A.ac_set_scan_config(a, chains=3)
+    with pytest.raises(A.AcError):
+        A.ac_set_scan_config(a, kernel=5)
+    # the device builder needs a device and the folded machine; unknown builders are refused
+    for kw in (dict(device=-1), dict(device=-1, machine=A.AC_MACHINE_PFAC)):
+        with pytest.raises(A.AcError) as e:
+            A.ac_build([b"AC"], builder=A.AC_BUILDER_DEVICE, **kw)
+        assert e.value.code == A.AC_EINVAL
+    with pytest.raises(A.AcError) as e:
+        A.ac_build([b"AC"], builder=9, device=-1)
+    assert e.value.code == A.AC_EINVAL
 
 
 def test_explicit_alphabet_order_sets_symbol_codes():
