@@ -255,7 +255,12 @@ AC_API int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, 
 /* Scan n symbols of `text` (fmt AC_U8 or AC_PACKED2; mem AC_HOST or
  * AC_DEVICE) and return the sorted matches and the counts in *out (host
  * arrays, release with ac_result_free). Synchronous: returns when the result
- * is on the host. Host text is copied to the device inside the call. */
+ * is on the host. Host text is copied to the device inside the call; a host
+ * text of 32 MiB or more (folded machine) is copied in pieces on a stream of
+ * the library's own, and each piece is scanned on `stream` as soon as it has
+ * landed (short rows, so that each piece spreads over the GPU), which hides
+ * the scan behind the host-to-device copy. Page-locked host memory lets the
+ * copies run asynchronously. */
 AC_API int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int mem,
             void *stream, ac_result *out);
 

@@ -128,6 +128,9 @@ struct ScanText {
     uint64_t n;             // symbols
     int fmt;
     uint64_t readable;      // bytes that may be read at d_text (>= the text's bytes; 0 = exactly those)
+    // rows [row_begin, row_end) of the text's row geometry only (row_end 0 = to the last row): a text
+    // scanned in pieces as it arrives, with the same row length in every launch
+    uint64_t row_begin = 0, row_end = 0;
 };
 
 struct ScanOut {
@@ -142,6 +145,7 @@ struct ScanOut {
 constexpr uint32_t kStageBytes = 32;   // bytes of one chain's text per pipeline stage
 
 int scan_smem_limit(int device);
+uint64_t scan_row_bytes(const ac_scan_config &cfg, int fmt, uint64_t readable);
 uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,

@@ -228,6 +228,78 @@ static int stage_text(const uint8_t *text, uint64_t nbytes, int mem, cudaStream_
     return AC_OK;
 }
 
+// Host texts of at least this many bytes are copied in pieces that overlap the scan.
+constexpr uint64_t kPipeMinBytes = 32ull << 20;
+
+// The library's copy stream of the current device (one per device, created on
+// first use; never destroyed).
+static cudaStream_t copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+
+// Copy host text[0, t.n) into d_text piece by piece on the copy stream and
+// scan each piece's rows on stream s as soon as the piece has landed: the
+// rows of one launch read the bytes before them (their warm-up) from pieces
+// copied earlier, and every launch uses the same row geometry, so the union
+// of the launches is exactly one scan of the text.
+static int pipelined_scan(const ac_automaton *a, const uint8_t *host, const uint8_t *d_text, const ScanText &t,
+                          const ScanOut &o, const ac_scan_config &cfg, cudaStream_t s) {
+    const uint64_t nbytes = text_bytes(t.n, t.fmt);
+    const uint64_t rb = scan_row_bytes(cfg, t.fmt, t.readable);
+    const uint64_t full_rows = t.readable / rb;
+    const uint64_t num_rows = full_rows + (nbytes > full_rows * rb ? 1 : 0);
+    const uint64_t piece_bytes = std::max<uint64_t>(16ull << 20, nbytes / 32);
+    const uint64_t piece_rows = std::max<uint64_t>(1, piece_bytes / rb);
+    cudaStream_t cs = copy_stream();
+    if (!cs) return set_error(AC_ECUDA, "ac_scan: no copy stream");
+    std::vector<cudaEvent_t> evs;
+    auto done = [&](int rc) {
+        // s waits for everything this call put on the copy stream (the text
+        // buffer is released in the order of s), also after an error
+        cudaEvent_t last;
+        if (cudaEventCreateWithFlags(&last, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(last, cs);
+            cudaStreamWaitEvent(s, last, 0);
+            cudaEventDestroy(last);
+        }
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+        return rc;
+    };
+    // the copy stream starts after the text buffer's allocation on s
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(AC_ECUDA, "ac_scan: event");
+    evs.push_back(start);
+    if (cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(cs, start, 0) != cudaSuccess)
+        return done(set_error(AC_ECUDA, "ac_scan: copy stream order"));
+    for (uint64_t r0 = 0; r0 < num_rows; r0 += piece_rows) {
+        const uint64_t r1 = std::min(num_rows, r0 + piece_rows);
+        const uint64_t b0 = r0 * rb, b1 = r1 == num_rows ? nbytes : std::min(nbytes, r1 * rb);
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return done(set_error(AC_ECUDA, "ac_scan: event"));
+        evs.push_back(ev);
+        if (b1 > b0 &&
+            cudaMemcpyAsync((void *)(d_text + b0), host + b0, b1 - b0, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            return done(set_error(AC_ECUDA, "ac_scan: text copy"));
+        if (cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess)
+            return done(set_error(AC_ECUDA, "ac_scan: piece order"));
+        ScanText piece = t;
+        piece.row_begin = r0;
+        piece.row_end = r1;
+        const int rc = launch_scan(a, piece, o, cfg, s);
+        if (rc) return done(rc);
+    }
+    return done(AC_OK);
+}
+
 }  // namespace acgb
 
 using namespace acgb;
@@ -438,8 +510,19 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         const uint64_t nbytes = text_bytes(n, fmt);
         const uint8_t *d_text = nullptr;
         uint64_t readable = 0;
-        int e = stage_text(text, nbytes, mem, s, sc, &d_text, &readable);
-        if (e) return e;
+        // a large host text is copied in pieces while the pieces already on
+        // the device are scanned (the host link, not the scan, sets the pace)
+        const bool pipe = mem == AC_HOST && a->machine == AC_MACHINE_DFA && nbytes >= kPipeMinBytes;
+        int e = AC_OK;
+        if (pipe) {
+            uint8_t *buf = (uint8_t *)sc.get((nbytes + 15) & ~15ull);
+            if (!buf) return set_error(AC_ENOMEM, "scan: device text buffer of %llu bytes", (unsigned long long)nbytes);
+            d_text = buf;
+            readable = nbytes;
+        } else {
+            e = stage_text(text, nbytes, mem, s, sc, &d_text, &readable);
+            if (e) return e;
+        }
         // counter, error word, counts
         unsigned long long *num = (unsigned long long *)sc.get(16 + (size_t)a->P * 8);
         if (!num) return set_error(AC_ENOMEM, "ac_scan: scratch");
@@ -448,6 +531,12 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         uint64_t cap = std::min<uint64_t>(n / 256 + 4096, 1ull << 26);
         ac_scan_config cfg;
         default_config(a, n, fmt, &cfg);
+        if (pipe && !a->cfg.row_len) {
+            // short rows, so that every piece spreads over all the SMs
+            const uint64_t warm = fmt == AC_U8 ? a->max_len : (a->max_len + 3) / 4;
+            const uint64_t rb = std::max<uint64_t>(128, 2 * ((warm + 31) / 32 * 32));
+            cfg.row_len = (uint32_t)std::min<uint64_t>(rb * (fmt == AC_U8 ? 1 : 4), 1u << 20);
+        }
         unsigned long long h_num[2];
         unsigned long long *keys = nullptr;
         for (int attempt = 0; attempt < 2; ++attempt) {
@@ -456,7 +545,10 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             CK(cudaMemsetAsync(num, 0, 16 + (size_t)a->P * 8, s), "ac_scan: memset");
             ScanText t{d_text, n, fmt, readable};
             ScanOut o{keys, cap, num, d_counts, err};
-            e = launch_scan(a, t, o, cfg, s);
+            if (pipe && attempt == 0)
+                e = pipelined_scan(a, text, d_text, t, o, cfg, s);
+            else
+                e = launch_scan(a, t, o, cfg, s);
             if (e) return e;
             CK(cudaMemcpyAsync(h_num, num, 16, cudaMemcpyDeviceToHost, s), "ac_scan: copy count");
             CK(cudaStreamSynchronize(s), "ac_scan: scan");

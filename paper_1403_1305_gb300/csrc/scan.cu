@@ -142,6 +142,19 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg) {
     return 256 + 128 + 128 + warps * kNS * slot_bytes_for(cfg.chains, bx) + warps * kNS * 8;
 }
 
+// Bytes per chain row of a scan under cfg (a multiple of kStageBytes, at
+// most the readable bytes rounded down to it; the text's row geometry).
+uint64_t scan_row_bytes(const ac_scan_config &cfg, int fmt, uint64_t readable) {
+    const uint32_t sym_per_byte = (fmt == AC_U8) ? 1 : 4;
+    uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
+    rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
+    if (rb > (1u << 24)) rb = 1u << 24;
+    const uint64_t rmax = readable / kStageBytes * kStageBytes;
+    if (rb > rmax) rb = rmax;
+    if (rb == 0) rb = kStageBytes;
+    return rb;
+}
+
 // ------------------------------------------------------------------ lean kernel
 bool lean_shape_ok(uint32_t threads, uint32_t chains) {
     return (threads == 1024 && (chains == 4 || chains == 2)) || (threads == 768 && chains == 4) ||
@@ -435,6 +448,8 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
     p.nsym = 0;
     p.full_rows = b.rows;
     p.num_rows = b.rows;
+    p.row_begin = 0;
+    p.row_end = b.rows;
     p.num_tiles = b.num_tiles;
     p.row_bytes = b.row_bytes;
     p.rows_per_tile = cfg.threads * cfg.chains;
@@ -490,13 +505,7 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     ScanPlan plan{};
     int rc = plan_lean(a, cfg, t.fmt, &plan);
     if (rc) return rc;
-    const uint32_t sym_per_byte = (t.fmt == AC_U8) ? 1 : 4;
-    uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
-    rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
-    if (rb > (1u << 24)) rb = 1u << 24;
-    const uint64_t rmax = readable / kStageBytes * kStageBytes;
-    if (rb > rmax) rb = rmax;
-    if (rb == 0) rb = kStageBytes;
+    const uint64_t rb = scan_row_bytes(cfg, t.fmt, readable);
 
     ScanParams p{};
     p.text = t.d_text;
@@ -507,6 +516,9 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     const uint64_t covered = p.full_rows * rb;
     p.tail_bytes = nbytes > covered ? (uint32_t)(nbytes - covered) : 0u;
     p.num_rows = p.full_rows + (p.tail_bytes ? 1 : 0);
+    p.row_begin = std::min(t.row_begin, p.num_rows);
+    p.row_end = t.row_end ? std::min(t.row_end, p.num_rows) : p.num_rows;
+    if (p.row_end <= p.row_begin) return AC_OK;
     p.rows_per_tile = cfg.threads * cfg.chains;
     p.K = a->K;
     p.sigma = a->sigma;
@@ -520,7 +532,7 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     p.smem_rows = plan.smem_rows;
     p.table_words = plan.table_words;
     memcpy(p.sym_of_byte, a->sym_of_byte, 256);
-    const uint64_t row_blocks = (p.num_rows + p.rows_per_tile - 1) / p.rows_per_tile;
+    const uint64_t row_blocks = (p.row_end - p.row_begin + p.rows_per_tile - 1) / p.rows_per_tile;
     p.num_tiles = row_blocks * a->K;
     if (p.full_rows >= (1ull << 31) || p.num_rows * rb >= (1ull << 40))
         return set_error(AC_ERANGE, "scan: text too long for the row tensor map");
@@ -548,7 +560,8 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device);
     // one machine: warps take blocks of 32 * chains rows, so a CTA needs only
     // one block; subset machines: CTA tiles of threads * chains rows
-    const uint64_t units = a->K == 1 ? (p.num_rows + 32ull * cfg.chains - 1) / (32ull * cfg.chains) : p.num_tiles;
+    const uint64_t units =
+        a->K == 1 ? (p.row_end - p.row_begin + 32ull * cfg.chains - 1) / (32ull * cfg.chains) : p.num_tiles;
     uint64_t grid = cfg.ctas ? cfg.ctas : (uint64_t)sms;
     if (grid > units) grid = units;
     fn<<<(unsigned)grid, cfg.threads, plan.smem, stream>>>(p, rows_map, tail_map);
@@ -575,13 +588,7 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     const uint64_t readable = std::max(nbytes, t.readable);
     if (readable < kStageBytes) return set_error(AC_EINVAL, "scan: text buffer shorter than one stage");
     if ((uintptr_t)t.d_text & 15) return set_error(AC_EINVAL, "scan: text must be 16-byte aligned");
-    const uint32_t sym_per_byte = (t.fmt == AC_U8) ? 1 : 4;
-    uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
-    rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
-    if (rb > (1u << 24)) rb = 1u << 24;
-    const uint64_t rmax = readable / kStageBytes * kStageBytes;
-    if (rb > rmax) rb = rmax;
-    if (rb == 0) rb = kStageBytes;
+    const uint64_t rb = scan_row_bytes(cfg, t.fmt, readable);
 
     ScanParams p{};
     p.text = t.d_text;
@@ -592,6 +599,9 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     const uint64_t covered = p.full_rows * rb;
     p.tail_bytes = nbytes > covered ? (uint32_t)(nbytes - covered) : 0u;
     p.num_rows = p.full_rows + (p.tail_bytes ? 1 : 0);
+    p.row_begin = std::min(t.row_begin, p.num_rows);
+    p.row_end = t.row_end ? std::min(t.row_end, p.num_rows) : p.num_rows;
+    if (p.row_end <= p.row_begin) return AC_OK;
     p.rows_per_tile = cfg.threads * cfg.chains;
     p.K = a->K;
     p.sigma = a->sigma;
@@ -603,7 +613,7 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     p.err = o.err;
     p.key_shift = (uint32_t)key_shift_for(a);
     memcpy(p.sym_of_byte, a->sym_of_byte, 256);
-    const uint64_t row_blocks = (p.num_rows + p.rows_per_tile - 1) / p.rows_per_tile;
+    const uint64_t row_blocks = (p.row_end - p.row_begin + p.rows_per_tile - 1) / p.rows_per_tile;
     p.num_tiles = row_blocks * a->K;
     if (p.full_rows >= (1ull << 31) || p.num_rows * rb >= (1ull << 40))
         return set_error(AC_ERANGE, "scan: text too long for the row tensor map");

@@ -69,6 +69,8 @@ struct ScanParams {
     uint64_t nsym;          // symbols
     uint64_t full_rows;     // rows of row_bytes entirely inside the text (2-D tensor map)
     uint64_t num_rows;      // full_rows, plus one if a partial last row exists
+    uint64_t row_begin;     // rows [row_begin, row_end) are this launch's (single text; a batch: all rows)
+    uint64_t row_end;
     uint64_t num_tiles;
     uint32_t row_bytes;     // multiple of kStageBytes
     uint32_t rows_per_tile; // warps * 32 * C
@@ -423,7 +425,7 @@ __device__ __forceinline__ bool chain_text(uint64_t row, const ScanParams &p, Ch
         ct.nsym = p.nsym;
         ct.vbase = 0;
         ct.cbase = 0;
-        return row < p.num_rows;
+        return row >= p.row_begin && row < p.row_end;
     }
     uint32_t lo = 0, hi = p.num_items;  // first item whose row_begin > row
     while (lo < hi) {
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(512, 1)
             tile_row0 = td.row0;
         } else {
             k = (uint32_t)(tile % p.K);
-            tile_row0 = (tile / p.K) * p.rows_per_tile;
+            tile_row0 = p.row_begin + (tile / p.K) * p.rows_per_tile;
         }
         const SubsetDev sd = p.subs[k];
         // rows staged in shared memory
@@ -514,8 +516,9 @@ __global__ void __launch_bounds__(512, 1)
         const uint32_t nW = (warm_bytes + BX - 1) / BX;
         const uint32_t nst = nW + p.row_bytes / BX;
         const uint64_t row0 = tile_row0 + (uint64_t)warp * 32 * C;
-        if (row0 >= p.num_rows) continue;
-        const bool tail_in_warp = !BATCH && p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
+        if (row0 >= p.row_end) continue;
+        const bool tail_in_warp = !BATCH && p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C &&
+                                  p.full_rows < p.row_end;
 
         // lane 0 issues one 2-D box per chain group (and the tail row's 1-D box)
         auto issue = [&](uint32_t s) {

@@ -158,7 +158,7 @@ __device__ __forceinline__ uint32_t lean_careful(uint32_t s_in, uint64_t row, in
                                              const ScanParams &p, const SubsetDev *sdp, const uint8_t *tab,
                                              const uint8_t *smap, uint32_t hot, uint32_t lane) {
     const SubsetDev &sd = *sdp;
-    const bool active = row < p.num_rows;
+    const bool active = row >= p.row_begin && row < p.row_end;
     const int64_t b0 = (int64_t)row * (int64_t)p.row_bytes + o;  // byte offset of the stage in the text
     uint32_t w[4] = {0, 0, 0, 0};
     if (active) {
@@ -274,10 +274,11 @@ __global__ void __launch_bounds__(NT, 1)
         // The partial last row of the text (if any) is read from global memory
         // by the careful walk at every stage (its bytes beyond the text end are
         // not in the row tensor map).
-        const bool tail_in_warp = p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C;
+        const bool tail_in_warp =
+            p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C && p.full_rows < p.row_end;
         // Stages [s_lo, s_hi) have every row of the warp inside the text (no
         // text edge, no partial row): their stages need no per-chain checks.
-        const uint64_t row_last = min(row0 + 32 * C, p.num_rows) - 1;
+        const uint64_t row_last = min(row0 + 32 * C, p.row_end) - 1;
         const uint64_t warm_total = (uint64_t)nW * BX;
         const uint32_t s_lo = row0 * L32 >= warm_total ? 0u : (uint32_t)(nW - row0 * L32 / BX);
         uint32_t s_hi = 0;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(NT, 1)
                     const uint64_t row = row0 + (uint64_t)jj * 32 + lane;
                     const int64_t b0 = (int64_t)row * L32 + o;
                     const int64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
-                    const bool dead = row >= p.num_rows || pos0 >= nsym;
+                    const bool dead = row >= p.row_end || pos0 >= nsym;
                     const bool before = !dead && pos0 + (int64_t)SYM <= 0;
                     const bool fast = !dead && pos0 >= 0 && pos0 + (int64_t)SYM <= nsym && row < p.full_rows;
                     const bool need = !dead && !before && (!fast || bad != 0 || (main_stage && (acc[0] & FLAG)));
@@ -457,10 +458,10 @@ __global__ void __launch_bounds__(NT, 1)
         const SubsetDev *sdp = p.subs;
         const uint32_t hot = hot_of(sdp);
         stage_table(sdp, hot);
-        const uint64_t blocks = (p.num_rows + 32 * C - 1) / (32 * C);
+        const uint64_t blocks = (p.row_end - p.row_begin + 32 * C - 1) / (32 * C);
         for (uint64_t t = (uint64_t)warp * gridDim.x + blockIdx.x; t < blocks && !aborted;
              t += (uint64_t)gridDim.x * nwarps)
-            run_rows(sdp, hot, t * 32 * C);
+            run_rows(sdp, hot, p.row_begin + t * 32 * C);
     } else {
         // subset machines: tiles of (threads * C rows, subset), subset index
         // fastest so concurrent CTAs share text rows in L2; the table is staged
@@ -475,8 +476,8 @@ __global__ void __launch_bounds__(NT, 1)
                 cur_k = (int)k;
             }
             if (aborted) continue;  // keeps taking part in the CTA barriers, does no work
-            const uint64_t row0 = (tile / p.K) * p.rows_per_tile + (uint64_t)warp * 32 * C;
-            if (row0 < p.num_rows) run_rows(sdp, hot, row0);
+            const uint64_t row0 = p.row_begin + (tile / p.K) * p.rows_per_tile + (uint64_t)warp * 32 * C;
+            if (row0 < p.row_end) run_rows(sdp, hot, row0);
         }
     }
     if (aborted && lane == 0) {
