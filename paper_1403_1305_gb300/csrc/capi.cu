@@ -255,7 +255,9 @@ static int pipelined_scan(const ac_automaton *a, const uint8_t *host, const uint
     const uint64_t rb = scan_row_bytes(cfg, t.fmt, t.readable);
     const uint64_t full_rows = t.readable / rb;
     const uint64_t num_rows = full_rows + (nbytes > full_rows * rb ? 1 : 0);
-    const uint64_t piece_bytes = std::max<uint64_t>(16ull << 20, nbytes / 32);
+    // a piece's scan takes at least one row block's latency (~0.1 ms); 8
+    // pieces of at least 32 MiB keep each scan within the next piece's copy
+    const uint64_t piece_bytes = std::max<uint64_t>(32ull << 20, (nbytes + 7) / 8);
     const uint64_t piece_rows = std::max<uint64_t>(1, piece_bytes / rb);
     cudaStream_t cs = copy_stream();
     if (!cs) return set_error(AC_ECUDA, "ac_scan: no copy stream");
