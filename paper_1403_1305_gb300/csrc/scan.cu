@@ -223,12 +223,11 @@ static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, a->device);
             const uint64_t chains = (uint64_t)sms * c.threads * c.chains;
             uint64_t want = (n + chains - 1) / chains;
-            // one machine: rows as short as twice the warm-up (at least one
-            // 32-byte block), so a short text still spreads over the SMs;
+            // one machine: all chains busy, rows down to one 32-byte block (a
+            // short text spreads over the SMs and each warp's walk is short);
             // subset machines: the general kernel's rule
             const uint64_t block = fmt == AC_U8 ? 32 : 128;
-            const uint64_t lo = a->K == 1 ? std::max<uint64_t>(2 * block, 2ull * a->max_len)
-                                          : std::max<uint64_t>(256, 8ull * a->max_len);
+            const uint64_t lo = a->K == 1 ? block : std::max<uint64_t>(256, 8ull * a->max_len);
             uint64_t L = std::max<uint64_t>(want, lo);
             if (L > (1u << 20)) L = 1u << 20;
             c.row_len = (uint32_t)L;

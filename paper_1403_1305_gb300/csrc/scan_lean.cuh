@@ -40,9 +40,9 @@ constexpr uint32_t kLeanBX = 16;  // text bytes per chain per stage
 __host__ __device__ constexpr uint32_t lean_slot_bytes(uint32_t C) { return C * 32u * kLeanBX + 128u; }
 
 // shared memory of a lean CTA besides the table: byte map, one staging slot
-// and one mbarrier per warp, alignment
+// and one mbarrier per warp, the table's mbarrier and state word, alignment
 __host__ __device__ constexpr uint32_t lean_stage_bytes(uint32_t threads, uint32_t C) {
-    return 256u + 128u + 128u + (threads / 32u) * (lean_slot_bytes(C) + 8u);
+    return 256u + 128u + 128u + 16u + (threads / 32u) * (lean_slot_bytes(C) + 8u);
 }
 
 // E16 lookup of entry (state u, symbol): sa = its shared address in the 16-bit
@@ -225,10 +225,13 @@ __global__ void __launch_bounds__(NT, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(stage + (size_t)nwarps * SLOT);
     const uint32_t my_stage = smem_addr(stage) + warp * SLOT;  // shared-window addresses
     const uint32_t my_bar = smem_addr(bars + warp);
+    uint64_t *tbars = bars + nwarps;  // the table's mbarrier, then its state word
 
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
     if (threadIdx.x == 0) {
-        for (uint32_t i = 0; i < nwarps; ++i) mbar_init(bars + i, 1);
+        for (uint32_t i = 0; i <= nwarps; ++i) mbar_init(bars + i, 1);  // one per warp, one for the table
+        // table copy state: [0] = the last copy landed, [1] = barrier phase | (a copy is late) << 1
+        reinterpret_cast<uint32_t *>(tbars + 1)[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -240,6 +243,11 @@ __global__ void __launch_bounds__(NT, 1)
     const int64_t nsym = (int64_t)p.nsym;
 
     // Stage subset k's table into shared memory (all threads of the CTA).
+    // Stage subset k's table into shared memory (all threads of the CTA). The
+    // escape-coded prefix is copied as it is by one bulk copy (the TMA engine
+    // streams it); the row-offset table is converted on the way, eight
+    // independent loads per thread in flight.
+    // (the table copy's state lives in shared memory, not in registers the scan loop would carry)
     auto stage_table = [&](const SubsetDev *sdp, uint32_t hot) {
         __syncthreads();  // every warp is done with the previous table
         if (LM == LEAN_SMEM32) {
@@ -247,18 +255,47 @@ __global__ void __launch_bounds__(NT, 1)
             const uint32_t words = hot * 4u;
             const uint32_t *gtab = sdp->table;
             uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
-            for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
-                const uint32_t e = __ldg(gtab + i);
-                t32[i] = ((e & kStateMask) << 4) | (e >> 31);
+            for (uint32_t base = threadIdx.x; base < words; base += blockDim.x * 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t i = base + k * blockDim.x;
+                    v[k] = i < words ? __ldg(gtab + i) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t i = base + k * blockDim.x;
+                    if (i < words) t32[i] = ((v[k] & kStateMask) << 4) | (v[k] >> 31);
+                }
             }
         } else {
-            const uint32_t halves = hot * 4u;  // 16-bit entries
-            const uint4 *src4 = reinterpret_cast<const uint4 *>(sdp->table_e16);
-            uint4 *dst4 = reinterpret_cast<uint4 *>(tab);
-            for (uint32_t i = threadIdx.x; i < halves / 8; i += blockDim.x) dst4[i] = __ldg(src4 + i);
-            uint16_t *t16 = reinterpret_cast<uint16_t *>(tab);
-            for (uint32_t i = (halves & ~7u) + threadIdx.x; i < halves; i += blockDim.x)
-                t16[i] = __ldg(sdp->table_e16 + i);
+            const uint32_t bytes = hot * 8u;      // 16-bit entries, 4 per row
+            const uint32_t bulk = bytes & ~15u;   // a bulk copy moves multiples of 16 bytes
+            const uint32_t tbar = smem_addr(tbars);
+            volatile uint32_t *tw = reinterpret_cast<volatile uint32_t *>(tbars + 1);
+            if (threadIdx.x == 0) {
+                fence_proxy_async();  // the generic reads of the previous table come first
+                uint32_t ok = 1;
+                if (bulk) {
+                    mbar_expect_s(tbar, bulk);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_addr(tab)),
+                        "l"(sdp->table_e16), "r"(bulk), "r"(tbar)
+                        : "memory");
+                }
+                if (bytes > bulk)  // the last 8 bytes (an odd row count)
+                    *reinterpret_cast<uint2 *>(tab + bulk) = __ldg(reinterpret_cast<const uint2 *>(
+                        reinterpret_cast<const uint8_t *>(sdp->table_e16) + bulk));
+                if (bulk) {
+                    const uint32_t st = tw[1];
+                    ok = wait_phase_s(tbar, st & 1u, p.err) ? 1u : 0u;
+                    tw[1] = ok ? (st ^ 1u) : (st | 2u);
+                }
+                tw[0] = ok;
+            }
+            __syncthreads();  // the table has landed (thread 0 saw the barrier's phase complete)
+            if (!tw[0]) aborted = true;
         }
         __syncthreads();
     };
@@ -484,6 +521,12 @@ __global__ void __launch_bounds__(NT, 1)
         // let a copy already issued by this warp land before the CTA exits (bounded)
         const uint64_t t0 = global_ns();
         while (!mbar_try_wait_s(my_bar, parity & 1u) && global_ns() - t0 < 100000000ull) {
+        }
+    }
+    if (threadIdx.x == 0) {  // the same for a table copy that was late
+        const uint32_t st = reinterpret_cast<volatile uint32_t *>(tbars + 1)[1];
+        const uint64_t t0 = global_ns();
+        while ((st & 2u) && !mbar_try_wait_s(smem_addr(tbars), st & 1u) && global_ns() - t0 < 100000000ull) {
         }
     }
 }
