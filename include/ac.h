@@ -152,10 +152,11 @@ typedef struct {
     uint32_t chains;
     uint64_t table2_bytes;   /* sum over subsets of the two-symbol tables (0 if not built) */
     int32_t scan_placement;  /* the table placement (AC_PLACE_SMEM, _HYBRID, _OPT or _HYBRID16) and symbols per */
-    uint32_t scan_stride;    /* lookup a scan of byte text would use with the current configuration; -1 and 0
+    uint32_t scan_stride;    /* lookup a scan of a long byte text (1 GiB; shorter texts may run the short-text
+                                kernel) would use with the current configuration; -1 and 0
                                 when not applicable (host-only automaton, failure-less machine) */
-    int32_t scan_kernel;     /* AC_KERNEL_GENERAL or AC_KERNEL_LEAN: the kernel such a scan runs (-1 when not
-                                applicable) */
+    int32_t scan_kernel;     /* AC_KERNEL_GENERAL, AC_KERNEL_LEAN or AC_KERNEL_SHORT: the kernel such a scan
+                                runs (-1 when not applicable) */
 } ac_stats_t;
 
 /* Read-only host view of one subset machine (valid until ac_free). States are
@@ -210,7 +211,8 @@ typedef struct {
 } ac_scan_config;
 
 /* Scan kernels (ac_scan_config.kernel). */
-#define AC_KERNEL_AUTO 0    /* the lean kernel where it applies, else the general one */
+#define AC_KERNEL_AUTO 0    /* the short-text kernel for short texts where it applies, else the lean kernel
+                               where it applies, else the general one */
 #define AC_KERNEL_GENERAL 1 /* every table placement, alphabet and stride; threads <= 512, chains 1, 2 or 4 */
 #define AC_KERNEL_LEAN 2    /* one-symbol scans of a 4-letter machine over ACGT bytes or packed text
                                (placement AUTO, SMEM or HYBRID16): the whole table in shared memory when it
@@ -218,6 +220,16 @@ typedef struct {
                                through L2; 16-byte stages; (threads, chains) in {(1024, 4), (1024, 2),
                                (768, 4), (512, 4)}, default (1024, 4). AC_EINVAL at scan time when it does
                                not apply. */
+#define AC_KERNEL_SHORT 3   /* short texts on one 4-letter machine (one subset, any 4-letter alphabet, u8 or
+                               packed text, placement AUTO, SMEM or HYBRID16): one thread per row of 16 to 64
+                               bytes (row_len; by default about 150,000 rows: 16 bytes up to 2.4 MB of text,
+                               longer rows above), its warm-up and row loaded straight into registers in one
+                               round trip; the whole table in shared memory when it fits in 96 KB (all of the
+                               SM's room with placement SMEM), else the escape-coded 16-bit prefix with the
+                               rest read through L2. threads a multiple of 32 in [64, 1024] (default 512),
+                               chains 1; the warm-up and the row at most nine 16-byte words. AC_KERNEL_AUTO
+                               takes it for texts of at most 8 Mi symbols when the configuration is otherwise
+                               untouched. AC_EINVAL at scan time when it does not apply. */
 
 /* ------------------------------------------------------------ automaton */
 
@@ -360,10 +372,19 @@ typedef struct {
     uint32_t num_streams;       /* launches in flight at once (0 = 2) */
     uint32_t max_wait_us;       /* how long the scheduler lets a partial batch wait for more arrivals
                                    (0 = none) */
-    uint64_t pinned_bytes;      /* page-locked host staging the server copies submitted texts into, so
-                                   their host->device copies run asynchronously (0 = 1 GiB); texts that do
-                                   not fit wait in ordinary host memory */
+    uint64_t pinned_bytes;      /* page-locked host staging the server copies submitted texts into when
+                                   they are not staged on the device (0 = 1 GiB); texts that fit neither
+                                   wait in ordinary host memory */
+    uint32_t staging;           /* AC_STAGE_DEVICE (0) or AC_STAGE_PINNED: where ac_serve_submit puts the
+                                   text until its batch runs */
 } ac_serve_opts;
+
+#define AC_STAGE_DEVICE 0 /* submit copies the text straight into device memory (one host->device copy on
+                             the calling thread's per-thread stream, finished before submit returns); at
+                             most device_mem_budget bytes of texts wait there, the rest go to the pinned
+                             slab */
+#define AC_STAGE_PINNED 1 /* submit copies the text into the page-locked slab; the batch's launch copies
+                             it to the device */
 
 /* Start a server over na resident automata (borrowed; they must outlive the
  * server). A scheduler thread admits requests by memory, coalesces them into
@@ -371,9 +392,10 @@ typedef struct {
 AC_API int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_opts *opts,
                     ac_server **out);
 
-/* Queue a request: scan host text[0..n) (copied before returning) with
- * automaton `automaton`. *ticket identifies it. AC_EBUSY when the queue is
- * full, AC_ERANGE when the text alone exceeds the memory budget. */
+/* Queue a request: scan host text[0..n) (copied before returning, into
+ * device memory or the pinned slab as opts.staging says) with automaton
+ * `automaton`. *ticket identifies it. AC_EBUSY when the queue is full,
+ * AC_ERANGE when the text alone exceeds the memory budget. */
 AC_API int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt,
                     uint64_t *ticket);
 

@@ -27,8 +27,9 @@ AC_HOST, AC_DEVICE = 0, 1
 AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL, AC_PLACE_OPT, AC_PLACE_HYBRID16 = 0, 1, 2, 3, 4, 5
 AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
 AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
-AC_KERNEL_AUTO, AC_KERNEL_GENERAL, AC_KERNEL_LEAN = 0, 1, 2
+AC_KERNEL_AUTO, AC_KERNEL_GENERAL, AC_KERNEL_LEAN, AC_KERNEL_SHORT = 0, 1, 2, 3
 AC_BUILDER_HOST, AC_BUILDER_DEVICE = 0, 1
+AC_STAGE_DEVICE, AC_STAGE_PINNED = 0, 1
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
@@ -91,7 +92,8 @@ class ac_batch_item(C.Structure):
 
 class ac_serve_opts(C.Structure):
     _fields_ = [("device_mem_budget", C.c_uint64), ("max_batch_items", C.c_uint32), ("max_queue", C.c_uint32),
-                ("num_streams", C.c_uint32), ("max_wait_us", C.c_uint32), ("pinned_bytes", C.c_uint64)]
+                ("num_streams", C.c_uint32), ("max_wait_us", C.c_uint32), ("pinned_bytes", C.c_uint64),
+                ("staging", C.c_uint32)]
 
 
 class ac_serve_stats_t(C.Structure):
@@ -412,9 +414,11 @@ class Server:
 
 
 def ac_serve_create(automata, device_mem_budget: int = 0, max_batch_items: int = 0, max_queue: int = 0,
-                    num_streams: int = 0, max_wait_us: int = 0, pinned_bytes: int = 0) -> Server:
+                    num_streams: int = 0, max_wait_us: int = 0, pinned_bytes: int = 0,
+                    staging: int = 0) -> Server:
     hs = (C.c_void_p * max(1, len(automata)))(*[a.h for a in automata])
-    opts = ac_serve_opts(device_mem_budget, max_batch_items, max_queue, num_streams, max_wait_us, pinned_bytes)
+    opts = ac_serve_opts(device_mem_budget, max_batch_items, max_queue, num_streams, max_wait_us, pinned_bytes,
+                         staging)
     h = C.c_void_p()
     _check(lib().ac_serve_create(hs, len(automata), C.byref(opts), C.byref(h)), "ac_serve_create")
     return Server(h, list(automata))

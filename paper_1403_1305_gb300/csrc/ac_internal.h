@@ -143,6 +143,15 @@ struct ScanOut {
 
 // Stage geometry shared by host planning and the kernels.
 constexpr uint32_t kStageBytes = 32;   // bytes of one chain's text per pipeline stage
+// Short-text kernel: rows of at most 64 bytes (by default about kShortRows
+// rows); the automatic choice takes it for texts of up to kShortAutoSymbols
+// symbols; its table room keeps two CTAs per SM.
+constexpr uint32_t kShortMaxRowBytes = 64;
+constexpr uint64_t kShortRows = 150000;
+constexpr uint64_t kShortAutoSymbols = 8ull << 20;
+constexpr uint32_t kShortSmemBytes = 96u << 10;
+uint32_t short_row_bytes(const ac_scan_config &cfg, int fmt);
+const char *short_unfit(const ac_automaton *a, const ac_scan_config &c, int fmt);
 
 int scan_smem_limit(int device);
 uint64_t scan_row_bytes(const ac_scan_config &cfg, int fmt, uint64_t readable);
@@ -156,8 +165,11 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
 // for the table, dynamic shared memory bytes.
 // table placements of the lean kernel (ScanPlan::mode when ScanPlan::lean)
 enum { kLeanSmem32 = 0, kLeanE16 = 1 };
+// table placements of the short-text kernel (ScanPlan::mode when ScanPlan::short_text)
+enum { kShortFull = 0, kShortE16 = 1 };
 struct ScanPlan {
     bool lean = false;  // the lean kernel (mode = kLeanSmem32 or kLeanE16)
+    bool short_text = false;  // the short-text kernel (mode = kShortFull or kShortE16)
     int mode = 0;
     uint32_t stride = 1;
     uint32_t smem_rows = 0;

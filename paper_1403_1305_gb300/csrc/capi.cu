@@ -398,27 +398,30 @@ int ac_stats(const ac_automaton *a, ac_stats_t *o) {
     o->num_subsets = a->K;
     o->sigma = a->sigma;
     o->max_len = a->max_len;
-    // the plan a scan of byte text with the current configuration would use
+    // the plan a scan of a long byte text (1 GiB) with the current configuration would use
     ScanPlan plan{};
     bool planned = false;
     if (a->device >= 0 && a->machine == AC_MACHINE_DFA) {
         ac_scan_config c{};
-        default_config(a, 1, AC_U8, &c);
+        default_config(a, 1ull << 30, AC_U8, &c);
         planned = plan_scan(a, c, AC_U8, &plan) == AC_OK;
     }
     // kernel modes of the plan: 0 all rows, 1 hybrid, 2 optimistic prefix, 3 16-bit prefix
     static const int32_t kPlacementOfMode[4] = {AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_OPT, AC_PLACE_HYBRID16};
     o->scan_placement = !planned ? -1
+                        : plan.short_text ? (plan.mode == kShortFull ? AC_PLACE_SMEM : AC_PLACE_HYBRID16)
                         : plan.lean ? (plan.mode == kLeanSmem32 ? AC_PLACE_SMEM : AC_PLACE_HYBRID16)
                                     : kPlacementOfMode[plan.mode & 3];
     o->scan_stride = planned ? plan.stride : 0;
-    o->scan_kernel = !planned ? -1 : plan.lean ? AC_KERNEL_LEAN : AC_KERNEL_GENERAL;
+    o->scan_kernel = !planned ? -1 : plan.short_text ? AC_KERNEL_SHORT : plan.lean ? AC_KERNEL_LEAN : AC_KERNEL_GENERAL;
     for (auto &s : a->subs) {
         o->states += s.states;
         o->table_bytes += (uint64_t)s.table.size() * 4;
         o->output_entries += s.out_ids.size();
         o->table2_bytes += (uint64_t)s.table2.size() * 4;
-        if (planned && plan.lean)
+        if (planned && plan.short_text)
+            o->smem_states += std::min<uint64_t>(plan.mode == kShortFull ? s.states : s.rows_e16, plan.smem_rows);
+        else if (planned && plan.lean)
             o->smem_states += std::min<uint64_t>(plan.mode == kLeanSmem32 ? s.states : s.rows_e16,
                                                  plan.smem_rows);
         else if (planned)
@@ -462,7 +465,7 @@ int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
         return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 1024");
     if (cfg->chains && cfg->chains != 1 && cfg->chains != 2 && cfg->chains != 4)
         return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
-    if (cfg->kernel > AC_KERNEL_LEAN) return set_error(AC_EINVAL, "ac_set_scan_config: unknown kernel %u", cfg->kernel);
+    if (cfg->kernel > AC_KERNEL_SHORT) return set_error(AC_EINVAL, "ac_set_scan_config: unknown kernel %u", cfg->kernel);
     if (cfg->stage_bytes && cfg->stage_bytes != 16 && cfg->stage_bytes != 32)
         return set_error(AC_EINVAL, "ac_set_scan_config: stage bytes must be 16 or 32");
     if (cfg->stride > 2) return set_error(AC_EINVAL, "ac_set_scan_config: stride must be 0, 1 or 2");
@@ -533,7 +536,7 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         uint64_t cap = std::min<uint64_t>(n / 256 + 4096, 1ull << 26);
         ac_scan_config cfg;
         default_config(a, n, fmt, &cfg);
-        if (pipe && !a->cfg.row_len) {
+        if (pipe && !a->cfg.row_len && cfg.kernel != AC_KERNEL_SHORT) {
             // short rows, so that every piece spreads over all the SMs
             const uint64_t warm = fmt == AC_U8 ? a->max_len : (a->max_len + 3) / 4;
             const uint64_t rb = std::max<uint64_t>(128, 2 * ((warm + 31) / 32 * 32));

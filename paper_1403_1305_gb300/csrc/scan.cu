@@ -146,6 +146,7 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg) {
 // most the readable bytes rounded down to it; the text's row geometry).
 uint64_t scan_row_bytes(const ac_scan_config &cfg, int fmt, uint64_t readable) {
     const uint32_t sym_per_byte = (fmt == AC_U8) ? 1 : 4;
+    if (cfg.kernel == AC_KERNEL_SHORT) return short_row_bytes(cfg, fmt);
     uint64_t rb = ((uint64_t)cfg.row_len + sym_per_byte - 1) / sym_per_byte;
     rb = (rb + kStageBytes - 1) / kStageBytes * kStageBytes;
     if (rb > (1u << 24)) rb = 1u << 24;
@@ -190,6 +191,36 @@ const char *lean_unfit(const ac_automaton *a, const ac_scan_config &c, int fmt) 
     return nullptr;
 }
 
+// Row bytes of a short-text scan: row_len symbols rounded up to 16-byte
+// words, one to four words (default one).
+uint32_t short_row_bytes(const ac_scan_config &cfg, int fmt) {
+    const uint64_t spb = (fmt == AC_U8) ? 1 : 4;
+    uint64_t rb = cfg.row_len ? ((uint64_t)cfg.row_len + spb - 1) / spb : 16;
+    rb = (rb + 15) / 16 * 16;
+    return (uint32_t)std::min<uint64_t>(rb, kShortMaxRowBytes);
+}
+
+// Why the short-text kernel cannot scan format fmt of `a` under
+// configuration c, or nullptr when it can.
+const char *short_unfit(const ac_automaton *a, const ac_scan_config &c, int fmt) {
+    if (a->machine != AC_MACHINE_DFA) return "it walks the folded machine only";
+    if (a->K != 1) return "it scans one machine (no pattern subsets)";
+    if (a->sigma != 4) return "it needs a 4-letter machine";
+    if (c.stride == 2) return "it uses the one-symbol table (stride 1)";
+    if (a->placement != AC_PLACE_AUTO && a->placement != AC_PLACE_SMEM && a->placement != AC_PLACE_HYBRID16)
+        return "it supports placements AUTO, SMEM and HYBRID16";
+    if (c.chains > 1) return "it runs one chain per thread";
+    if (c.threads && (c.threads < 64 || c.threads > 1024 || c.threads % 32))
+        return "threads per CTA must be a multiple of 32 in [64, 1024]";
+    const uint64_t spb = (fmt == AC_U8) ? 1 : 4;
+    if (c.row_len && (c.row_len + spb - 1) / spb > kShortMaxRowBytes) return "rows are at most 64 bytes of text";
+    if (a->h_desc.empty() || a->h_desc[0].states >= (1u << 28)) return "it needs fewer than 2^28 states";
+    const uint64_t warm_bytes = (fmt == AC_U8) ? a->h_desc[0].warm : (a->h_desc[0].warm + 3ull) / 4;
+    if ((warm_bytes + 15) / 16 + short_row_bytes(c, fmt) / 16 > kern::kShortMaxWords)
+        return "the warm-up (longest pattern - 1 symbols) and the row exceed nine 16-byte words";
+    return nullptr;
+}
+
 static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int fmt, ac_scan_config *cfg);
 
 // Would the general kernel's automatic plan use two symbols per lookup for
@@ -211,6 +242,35 @@ void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *
 // configuration c whose zero fields take their defaults.
 static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int fmt, ac_scan_config *cfg) {
     const ac_scan_config given = c;
+    // a short text on one 4-letter machine: one thread per 16-byte row, each
+    // thread's window loaded in one round trip (the pipelined kernels pay a
+    // copy round trip per 16-byte stage and leave most of the GPU idle)
+    const uint64_t nbytes = (fmt == AC_U8) ? n : (n + 3) / 4;
+    const bool untouched = !c.row_len && !c.threads && !c.chains && !c.ctas && !c.stage_bytes;
+    if (a->device >= 0 &&
+        (c.kernel == AC_KERNEL_SHORT ||
+         (c.kernel == AC_KERNEL_AUTO && untouched && n <= kShortAutoSymbols && !short_unfit(a, c, fmt)))) {
+        // (values given for the short kernel stay as they are: the launch refuses those it cannot run)
+        c.kernel = AC_KERNEL_SHORT;
+        if (!c.threads) c.threads = 512;
+        if (!c.chains) c.chains = 1;
+        if (!c.stride) c.stride = 1;
+        if (!c.row_len) {
+            // about kShortRows rows (the GPU holds ~300k threads): rows of 16
+            // bytes while the text is short (each thread's walk, mostly
+            // warm-up, is the latency), longer ones as it grows (fewer warm-up
+            // lookups in all); warm-up and row within the window
+            const uint64_t warm_bytes =
+                a->h_desc.empty() ? 0 : (fmt == AC_U8 ? a->h_desc[0].warm : (a->h_desc[0].warm + 3ull) / 4);
+            const uint64_t words_left = kern::kShortMaxWords - std::min<uint64_t>(kern::kShortMaxWords - 1,
+                                                                                  (warm_bytes + 15) / 16);
+            uint64_t rb = (nbytes / kShortRows + 15) / 16 * 16;
+            rb = std::min<uint64_t>(std::max<uint64_t>(rb, 16), std::min<uint64_t>(kShortMaxRowBytes, 16 * words_left));
+            c.row_len = (uint32_t)rb * (fmt == AC_U8 ? 1 : 4);
+        }
+        *cfg = c;
+        return;
+    }
     const bool lean_ok = c.kernel != AC_KERNEL_GENERAL && a->device >= 0 && !lean_unfit(a, c, fmt) &&
                          !(c.kernel == AC_KERNEL_AUTO && c.stride == 0 && general_picks_stride2(a, fmt));
     if (lean_ok) {
@@ -316,7 +376,39 @@ static int plan_lean(const ac_automaton *a, const ac_scan_config &cfg, int fmt, 
     return AC_OK;
 }
 
+// Short-text plan: the whole table in shared memory when it fits in the
+// room that leaves two CTAs per SM (all of the SM's room with placement
+// SMEM), else the longest escape-coded 16-bit prefix that fits there.
+static int plan_short(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out) {
+    if (const char *why = short_unfit(a, cfg, fmt)) return set_error(AC_EINVAL, "scan: short-text kernel: %s", why);
+    const int limit = scan_smem_limit(a->device);
+    uint64_t room = (uint64_t)std::max(0, limit - 512);
+    if (a->placement != AC_PLACE_SMEM) room = std::min<uint64_t>(room, kShortSmemBytes);
+    if (a->smem_cap_bytes && a->smem_cap_bytes < room) room = a->smem_cap_bytes;
+    if (cfg.smem_table_bytes && cfg.smem_table_bytes < room) room = cfg.smem_table_bytes;
+    const SubsetDev &d = a->h_desc[0];
+    ScanPlan pl{};
+    pl.short_text = true;
+    pl.stride = 1;
+    if ((uint64_t)d.states * 16 <= room && a->placement != AC_PLACE_HYBRID16) {
+        pl.mode = kern::SHORT_FULL;
+        pl.smem_rows = d.states;
+        pl.table_words = d.states * 4;
+    } else {
+        if (a->placement == AC_PLACE_SMEM)
+            return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory", d.states);
+        if (!d.table_e16) return set_error(AC_EINVAL, "scan: short-text kernel: the 16-bit prefix is missing");
+        pl.mode = kern::SHORT_E16;
+        pl.smem_rows = (uint32_t)std::min<uint64_t>(d.rows_e16, room / 8);
+        pl.table_words = (pl.smem_rows * 2 + 3) & ~3u;
+    }
+    pl.smem = (size_t)pl.table_words * 4 + 256;
+    *out = pl;
+    return AC_OK;
+}
+
 int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out) {
+    if (cfg.kernel == AC_KERNEL_SHORT) return plan_short(a, cfg, fmt, out);
     if (cfg.kernel == AC_KERNEL_LEAN) return plan_lean(a, cfg, fmt, out);
     uint32_t max_states = 0, max_rows16 = 0;
     bool has16 = a->sigma == 4 && !a->h_desc.empty();
@@ -569,9 +661,60 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     return AC_OK;
 }
 
+// One thread per row of rb bytes; rows [row_begin, row_end) of ceil(bytes / rb).
+static int launch_short(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
+                        cudaStream_t stream) {
+    const uint64_t nbytes = (t.fmt == AC_U8) ? t.n : (t.n + 3) / 4;
+    if (nbytes == 0) return AC_OK;
+    if ((uintptr_t)t.d_text & 15) return set_error(AC_EINVAL, "scan: text must be 16-byte aligned");
+    ScanPlan plan{};
+    int rc = plan_short(a, cfg, t.fmt, &plan);
+    if (rc) return rc;
+    const uint32_t rb = short_row_bytes(cfg, t.fmt);
+    const uint32_t threads = cfg.threads ? cfg.threads : 512;
+
+    ScanParams p{};
+    p.text = t.d_text;
+    p.nbytes = nbytes;
+    p.nsym = t.n;
+    p.row_bytes = rb;
+    p.num_rows = (nbytes + rb - 1) / rb;
+    p.full_rows = nbytes / rb;
+    p.row_begin = std::min(t.row_begin, p.num_rows);
+    p.row_end = t.row_end ? std::min(t.row_end, p.num_rows) : p.num_rows;
+    if (p.row_end <= p.row_begin) return AC_OK;
+    p.K = 1;
+    p.sigma = a->sigma;
+    p.subs = a->d_desc;
+    p.keys = o.keys;
+    p.cap = o.cap;
+    p.num = o.num;
+    p.counts = o.counts;
+    p.err = o.err;
+    p.key_shift = (uint32_t)key_shift_for(a);
+    p.smem_rows = plan.smem_rows;
+    p.table_words = plan.table_words;
+    memcpy(p.sym_of_byte, a->sym_of_byte, 256);
+    const uint64_t grid = (p.row_end - p.row_begin + threads - 1) / threads;
+    if (grid >= (1ull << 31)) return set_error(AC_ERANGE, "scan: text too long for the short-text kernel");
+    const uint64_t warm_bytes = (t.fmt == AC_U8) ? a->h_desc[0].warm : (a->h_desc[0].warm + 3ull) / 4;
+    const uint32_t words = (uint32_t)((warm_bytes + 15) / 16 + rb / 16);
+    kern::ShortFn fn = t.fmt == AC_PACKED2 ? (plan.mode == kern::SHORT_FULL ? kern::short_packed_full(words)
+                                                                            : kern::short_packed_e16(words))
+                                           : (plan.mode == kern::SHORT_FULL ? kern::short_u8_full(words)
+                                                                            : kern::short_u8_e16(words));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
+    fn<<<(unsigned)grid, threads, plan.smem, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(AC_ECUDA, "scan launch: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg_in,
                 cudaStream_t stream) {
     if (a->machine == AC_MACHINE_PFAC) return launch_pfac(a, t, o, cfg_in, stream);
+    if (cfg_in.kernel == AC_KERNEL_SHORT) return launch_short(a, t, o, cfg_in, stream);
     if (cfg_in.kernel == AC_KERNEL_LEAN) return launch_lean(a, t, o, cfg_in, stream);
     ac_scan_config cfg = cfg_in;
     if (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)

@@ -1,0 +1,161 @@
+// The short-text scan: one thread per row of one to four 16-byte words, for
+// texts too short to keep the GPU busy with the pipelined kernels' rows.
+//
+// It computes exactly what the lean and general kernels compute -- the
+// folded AC-opt machine of Section III walked one symbol per lookup, the
+// output of Section II.A reported at every flagged state, rows of the
+// input-focused split (Section III) each preceded by a warm-up of longest
+// pattern - 1 symbols walked from the root -- for one 4-letter machine.
+//
+// The pipelined kernels stage each chain's row through shared memory 16
+// bytes at a time, so a launch costs one copy round trip per stage even when
+// rows are a few stages long. Here every thread loads its whole window
+// (warm-up words and row words, at most nine 16-byte words) straight into
+// registers with vector loads issued before the table is staged; a launch
+// is one memory round trip and one walk of (warm-up + row) symbols per
+// thread, and every warp of the grid walks at once.
+//
+//  * SHORT_FULL: the whole table (next | output bit, 16 bytes a state)
+//    copied into shared memory as it is.
+//  * SHORT_E16: the escape-coded 16-bit breadth-first prefix in shared
+//    memory (the lean kernel's LEAN_E16 table), the rest read through L2.
+//
+// Bytes are mapped to symbols through the machine's symbol map, so any
+// 4-letter alphabet works; a byte outside the alphabet sends the walk to the
+// root (Section II.A: no pattern contains it).
+#include "ac_internal.h"
+#include "scan_kernel.cuh"
+
+namespace acgb {
+namespace kern {
+
+// Symbol i (0 <= i < 16 * symbols per byte) of a 16-byte word.
+template <int FMT>
+__device__ __forceinline__ uint32_t word_symbol(const uint4 &v, uint32_t i, const uint8_t *smap) {
+    constexpr uint32_t PER = (FMT == FMT_U8) ? 4 : 16;  // symbols per 32-bit word
+    const uint32_t e = i / PER, b = i % PER;
+    const uint32_t x = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+    return (FMT == FMT_U8) ? (uint32_t)smap[(x >> (8 * b)) & 0xffu] : (x >> (2 * b)) & 3u;
+}
+
+// One lookup: the entry (next | output bit) of state s on symbol c; the root
+// for a symbol outside the alphabet.
+template <int SM>
+__device__ __forceinline__ uint32_t short_step(uint32_t s, uint32_t c, const uint8_t *tab, uint32_t hot,
+                                               const uint32_t *gtab) {
+    if (c >= 4u) return 0u;
+    if (SM == SHORT_FULL) return reinterpret_cast<const uint32_t *>(tab)[s * 4u + c];
+    uint32_t nv = kEsc16;
+    if (s < hot) nv = reinterpret_cast<const uint16_t *>(tab)[s * 4u + c];
+    if (nv == kEsc16) nv = __ldg(gtab + (size_t)s * 4u + c);
+    return nv;
+}
+
+// MAXW: words of the window a thread holds (warm-up + row words <= MAXW).
+template <int FMT, int SM, int MAXW>
+__global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ ScanParams p) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const SubsetDev &sd = *p.subs;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warm_bytes = (FMT == FMT_U8) ? sd.warm : (sd.warm + 3) / 4;
+    const uint32_t nw_warm = (warm_bytes + 15) / 16;
+    const uint32_t nw = nw_warm + p.row_bytes / 16;  // <= MAXW (host-checked)
+    const uint64_t row = p.row_begin + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = row < p.row_end;
+    const int64_t nbytes = (int64_t)p.nbytes;
+    const int64_t b0 = (int64_t)row * p.row_bytes - 16 * (int64_t)nw_warm;  // first byte of the window
+
+    // The window into registers; the loads stay in flight while the table is staged.
+    uint4 w[MAXW];
+#pragma unroll
+    for (int k = 0; k < MAXW; ++k) {
+        w[k] = make_uint4(0, 0, 0, 0);
+        const int64_t b = b0 + 16 * (int64_t)k;
+        if (active && (uint32_t)k < nw) {
+            if (b >= 0 && b + 16 <= nbytes) {
+                w[k] = __ldg(reinterpret_cast<const uint4 *>(p.text + b));  // 16-byte aligned
+            } else if (b + 16 > 0 && b < nbytes) {  // a text edge inside the word
+                uint32_t v[4] = {0, 0, 0, 0};
+                for (int j = 0; j < 16; ++j)
+                    if (b + j >= 0 && b + j < nbytes) v[j >> 2] |= (uint32_t)__ldg(p.text + b + j) << (8 * (j & 3));
+                w[k] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+
+    // The table (and the symbol map) into shared memory.
+    const uint32_t tbytes = (SM == SHORT_FULL) ? sd.states * 16u : p.smem_rows * 8u;
+    uint8_t *tab = smem;
+    uint8_t *smap = smem + ((tbytes + 15) & ~15u);
+    {
+        const uint4 *src = (SM == SHORT_FULL) ? reinterpret_cast<const uint4 *>(sd.table)
+                                              : reinterpret_cast<const uint4 *>(sd.table_e16);
+        // asynchronous 16-byte copies: no registers held, every copy of the
+        // thread in flight at once
+        const uint32_t n16 = tbytes / 16;
+        const uint32_t dst0 = smem_addr(tab);
+        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + 16 * i), "l"(src + i) : "memory");
+        if ((tbytes & 15) && threadIdx.x == 0)  // an odd row count of the 16-bit prefix: its last 8 bytes
+            *reinterpret_cast<uint2 *>(tab + (tbytes & ~15u)) =
+                __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(src) + (tbytes & ~15u)));
+        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+
+    // The walk, one word at a time (the window shifts down one word per
+    // step): warm-up words from the root (positions before the text start
+    // keep it there), then the row's words. A row word in which some lane of
+    // the warp meets a flagged state is walked again by the warp, symbol by
+    // symbol, emitting the outputs.
+    const uint32_t hot = p.smem_rows;
+    constexpr uint32_t SYM = (FMT == FMT_U8) ? 16 : 64;  // symbols per word
+    const int64_t nsym = (int64_t)p.nsym;
+    uint32_t s = 0;
+#pragma unroll 1
+    for (uint32_t k = 0; k < nw; ++k) {
+        const uint4 cur = w[0];
+#pragma unroll
+        for (int j = 0; j + 1 < MAXW; ++j) w[j] = w[j + 1];
+        const int64_t pos0 = (b0 + 16 * (int64_t)k) * (SYM / 16);
+        const uint32_t s_in = s;
+        uint32_t acc = 0;
+        // 16 symbols per inner pass: one pass for bytes, four for packed text
+#pragma unroll 1
+        for (uint32_t q = 0; q < SYM; q += 16) {
+#pragma unroll
+            for (uint32_t i = 0; i < 16; ++i) {
+                const int64_t pos = pos0 + q + i;
+                const uint32_t nv = short_step<SM>(s, word_symbol<FMT>(cur, q + i, smap), tab, hot, sd.table);
+                const bool live = active && pos >= 0 && pos < nsym;
+                s = live ? (nv & kStateMask) : 0u;
+                acc |= live ? nv : 0u;
+            }
+        }
+        if (k >= nw_warm && __any_sync(kFull, (acc & kFlag) != 0)) {
+            s = s_in;
+#pragma unroll 1
+            for (uint32_t i = 0; i < SYM; ++i) {
+                const int64_t pos = pos0 + i;
+                const uint32_t nv = short_step<SM>(s, word_symbol<FMT>(cur, i, smap), tab, hot, sd.table);
+                const bool live = active && pos >= 0 && pos < nsym;
+                s = live ? (nv & kStateMask) : 0u;
+                emit_warp(live && (nv & kFlag), s, (uint64_t)(pos < 0 ? 0 : pos), 0, sd, p, lane);
+            }
+        }
+    }
+}
+
+template <int FMT, int SM>
+ShortFn pick_short(uint32_t words) {
+    return words <= 5 ? short_kernel<FMT, SM, 5> : short_kernel<FMT, SM, kShortMaxWords>;
+}
+
+ShortFn short_u8_full(uint32_t words) { return pick_short<FMT_U8, SHORT_FULL>(words); }
+ShortFn short_u8_e16(uint32_t words) { return pick_short<FMT_U8, SHORT_E16>(words); }
+ShortFn short_packed_full(uint32_t words) { return pick_short<FMT_P2, SHORT_FULL>(words); }
+ShortFn short_packed_e16(uint32_t words) { return pick_short<FMT_P2, SHORT_E16>(words); }
+
+}  // namespace kern
+}  // namespace acgb

@@ -1,6 +1,8 @@
 // Serving: a request loop over resident automata with continuous batching.
 //
-// ac_serve_submit copies a request's text and queues it. One worker thread
+// ac_serve_submit copies a request's text (into device memory, or into a
+// page-locked slab from which the batch's launch copies it) and queues it.
+// One worker thread
 // per CUDA stream takes queued requests in arrival order as long as they fit
 // in the device-memory budget (and at most max_batch_items of them, waiting
 // up to max_wait_us for more arrivals when the batch is small), runs them as
@@ -30,11 +32,12 @@ struct Request {
     int fmt;
     uint64_t n;
     uint64_t budget_bytes;  // device memory the request is charged while in flight
+    uint8_t *staged = nullptr;  // copy in device memory, or
     uint8_t *pinned = nullptr;  // copy in the page-locked slab, or
     std::vector<uint8_t> text;  // copy in ordinary host memory
-    uint64_t slab_off = 0, slab_len = 0;
+    uint64_t slab_off = 0, slab_len = 0, staged_len = 0;
     Clock::time_point t_submit;
-    const uint8_t *data() const { return pinned ? pinned : text.data(); }
+    const uint8_t *data() const { return staged ? staged : pinned ? pinned : text.data(); }
 };
 
 // First-fit allocator over the server's page-locked slab (16-byte granules).
@@ -96,6 +99,7 @@ struct ac_server {
     std::unordered_set<uint64_t> outstanding;  // issued, not yet handed back
     uint64_t next_ticket = 1;
     uint64_t mem_in_use = 0;
+    uint64_t staged_bytes = 0;  // texts waiting in device memory
     bool stopping = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
@@ -150,19 +154,36 @@ void worker_loop(ac_server *s, int w) {
             s->items_launched += batch.size();
         }
         if (batch.empty()) continue;
-        std::vector<ac_batch_item> items(batch.size());
-        for (size_t i = 0; i < batch.size(); ++i)
-            items[i] = ac_batch_item{batch[i]->automaton, batch[i]->fmt, batch[i]->data(), batch[i]->n};
+        // one launch per staging kind: device-staged texts, then host ones
         std::vector<ac_result> outs(batch.size());
-        const int rc = ac_scan_batch(s->as.data(), (uint32_t)s->as.size(), items.data(), (uint32_t)items.size(),
-                                     AC_HOST, 0, st, outs.data());
+        std::vector<int> rcs(batch.size(), AC_OK);
+        for (int mem : {AC_DEVICE, AC_HOST}) {
+            std::vector<ac_batch_item> items;
+            std::vector<size_t> at;
+            for (size_t i = 0; i < batch.size(); ++i)
+                if ((batch[i]->staged != nullptr) == (mem == AC_DEVICE)) {
+                    items.push_back(ac_batch_item{batch[i]->automaton, batch[i]->fmt, batch[i]->data(), batch[i]->n});
+                    at.push_back(i);
+                }
+            if (items.empty()) continue;
+            std::vector<ac_result> part(items.size());
+            const int rc = ac_scan_batch(s->as.data(), (uint32_t)s->as.size(), items.data(), (uint32_t)items.size(),
+                                         mem, 0, st, part.data());
+            for (size_t j = 0; j < at.size(); ++j) {
+                outs[at[j]] = part[j];
+                rcs[at[j]] = rc;
+            }
+        }
+        for (Request *r : batch)
+            if (r->staged) acgb::dev_free(r->staged, st);  // after the batch's work on st
         const auto now = Clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
             for (size_t i = 0; i < batch.size(); ++i) {
                 Request *r = batch[i];
-                s->done[r->ticket] = Done{outs[i], rc};
+                s->done[r->ticket] = Done{outs[i], rcs[i]};
                 s->mem_in_use -= r->budget_bytes;
+                s->staged_bytes -= r->staged_len;
                 s->completed++;
                 s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
                 if (r->pinned) s->slab.release(r->slab_off, r->slab_len);
@@ -172,6 +193,15 @@ void worker_loop(ac_server *s, int w) {
         s->cv_done.notify_all();
         s->cv_work.notify_all();
     }
+}
+
+// Release a device-staged text from a thread whose current device may differ.
+void free_staged(ac_server *s, uint8_t *d) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    acgb::dev_free(d, cudaStreamPerThread);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
 }
 
 int take_result(ac_server *s, uint64_t ticket, ac_result *out) {
@@ -209,6 +239,8 @@ int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_o
     for (uint32_t k = 0; k < na; ++k)
         if (!as[k] || as[k]->device < 0 || as[k]->device != as[0]->device)
             return set_error(AC_EINVAL, "ac_serve_create: automata must be built on one device");
+    if (opts && opts->staging != AC_STAGE_DEVICE && opts->staging != AC_STAGE_PINNED)
+        return set_error(AC_EINVAL, "ac_serve_create: unknown staging %u", opts->staging);
     ac_server *s = new (std::nothrow) ac_server();
     if (!s) return set_error(AC_ENOMEM, "ac_serve_create: host allocation");
     s->as.assign(as, as + na);
@@ -264,20 +296,51 @@ int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint6
     r->budget_bytes = charge;
     r->t_submit = Clock::now();
     const uint64_t nbytes = fmt == AC_U8 ? n : (n + 3) / 4;
+    bool to_device = false;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->pending.size() >= s->opts.max_queue) {
             delete r;
             return set_error(AC_EBUSY, "ac_serve_submit: queue full (%u requests)", s->opts.max_queue);
         }
-        if (nbytes && s->slab.alloc(nbytes, &r->slab_off)) {
+        if (nbytes && s->opts.staging == AC_STAGE_DEVICE && s->staged_bytes + nbytes <= s->opts.device_mem_budget) {
+            s->staged_bytes += nbytes;  // reserved; returned below if the copy cannot be made
+            r->staged_len = nbytes;
+            to_device = true;
+        } else if (nbytes && s->slab.alloc(nbytes, &r->slab_off)) {
             r->pinned = s->slab.base + r->slab_off;
             r->slab_len = nbytes;
         }
     }
+    if (to_device) {
+        // the copy ends before submit returns, so the caller may reuse text at once
+        int prev = -1;
+        cudaGetDevice(&prev);
+        bool ok = prev == s->device || cudaSetDevice(s->device) == cudaSuccess;
+        uint8_t *d = ok ? (uint8_t *)acgb::dev_alloc(nbytes, cudaStreamPerThread) : nullptr;
+        ok = d && cudaMemcpyAsync(d, text, nbytes, cudaMemcpyHostToDevice, cudaStreamPerThread) == cudaSuccess &&
+             cudaStreamSynchronize(cudaStreamPerThread) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (d) acgb::dev_free(d, cudaStreamPerThread);
+            d = nullptr;
+        }
+        if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+        if (d) {
+            r->staged = d;
+        } else {  // no device memory at the moment: wait in host memory instead
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->staged_bytes -= nbytes;
+            r->staged_len = 0;
+            if (s->slab.alloc(nbytes, &r->slab_off)) {
+                r->pinned = s->slab.base + r->slab_off;
+                r->slab_len = nbytes;
+            }
+        }
+    }
     if (r->pinned) {
         memcpy(r->pinned, text, nbytes);  // outside the lock: the range is ours
-    } else {
+    } else if (!r->staged) {
         try {
             r->text.assign(text, text + nbytes);
         } catch (...) {
@@ -290,6 +353,10 @@ int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint6
         if (s->stopping || s->pending.size() >= s->opts.max_queue) {
             const bool stopping = s->stopping;
             if (r->pinned) s->slab.release(r->slab_off, r->slab_len);
+            if (r->staged) {
+                free_staged(s, r->staged);
+                s->staged_bytes -= r->staged_len;
+            }
             delete r;
             return stopping ? set_error(AC_EINVAL, "ac_serve_submit: server is stopping")
                             : set_error(AC_EBUSY, "ac_serve_submit: queue full (%u requests)", s->opts.max_queue);

@@ -78,6 +78,11 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
     const uint32_t lean_shapes[4][2] = {{1024, 4}, {1024, 2}, {768, 4}, {512, 4}};
     for (int li = 0; li < 4 && rc == AC_OK; ++li)
         try_shape(AC_KERNEL_LEAN, lean_shapes[li][0], lean_shapes[li][1], 16);
+    // the short-text kernel for texts up to 16 MiB (one thread per 16-byte row)
+    if (nbytes <= (16ull << 20)) {
+        const uint32_t short_threads[3] = {256, 512, 1024};
+        for (int si = 0; si < 3 && rc == AC_OK; ++si) try_shape(AC_KERNEL_SHORT, short_threads[si], 1, 0);
+    }
     // 2. shared-memory table size (the rest goes through L1/L2)
     const uint32_t caps[5] = {0, 96u << 10, 48u << 10, 16u << 10, 4u << 10};
     ac_scan_config base = best;
@@ -97,7 +102,7 @@ extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int f
         for (uint32_t stride = 1; stride <= 2 && rc == AC_OK; ++stride) {
             ac_scan_config c = base;
             c.stride = stride;
-            if (stride == 2 && c.kernel == AC_KERNEL_LEAN) {
+            if (stride == 2 && c.kernel != AC_KERNEL_GENERAL) {
                 // two symbols per lookup run on the general kernel with its default shape
                 a->cfg = ac_scan_config{};
                 a->cfg.stride = 2;

@@ -3,8 +3,10 @@
 The same requests are scanned alone (ac_scan) and submitted together to a
 server that coalesces them into batched launches on several streams; every
 result must be identical in both cases and equal to the oracle. Also checked:
-poll/wait semantics, refusal when the queue is full or a text exceeds the
-memory budget, and a server destroyed with requests still queued.
+texts staged in device memory or in the pinned slab, and batches that mix
+both (the device share of the budget spent); poll/wait semantics, refusal
+when the queue is full or a text exceeds the memory budget, an unknown
+staging mode, and a server destroyed with requests still queued.
 """
 import numpy as np
 import pytest
@@ -55,13 +57,15 @@ def requests(rng, kinds, count, lo=1 << 10, hi=1 << 20):
     return out
 
 
-@pytest.mark.parametrize("streams,max_items", [(1, 1), (2, 8), (3, 256)])
-def test_alone_and_in_the_mix_are_identical(fleet, streams, max_items):
+@pytest.mark.parametrize("streams,max_items,staging", [(1, 1, A.AC_STAGE_DEVICE), (2, 8, A.AC_STAGE_DEVICE),
+                                                       (3, 256, A.AC_STAGE_DEVICE), (2, 8, A.AC_STAGE_PINNED)])
+def test_alone_and_in_the_mix_are_identical(fleet, streams, max_items, staging):
     sets, autos, kinds, machines = fleet
     rng = np.random.default_rng(52 + streams)
     reqs = requests(rng, kinds, 60)
     alone = [A.ac_scan(autos[k], t) for k, t in reqs]
-    srv = A.ac_serve_create(autos, num_streams=streams, max_batch_items=max_items, max_wait_us=200)
+    srv = A.ac_serve_create(autos, num_streams=streams, max_batch_items=max_items, max_wait_us=200,
+                            staging=staging)
     tickets = [A.ac_serve_submit(srv, k, t) for k, t in reqs]
     mixed = [A.ac_serve_wait(srv, tk, 120_000) for tk in tickets]
     st = A.ac_serve_stats(srv)
@@ -128,3 +132,26 @@ def test_destroy_with_queued_requests(fleet):
     for k, t in requests(rng, kinds, 20):
         A.ac_serve_submit(srv, k, t)
     A.ac_serve_destroy(srv)          # drains the queue and returns
+
+
+def test_device_staging_overflows_to_the_slab(fleet):
+    """A 6 MiB budget holds a few 1 MiB texts in device memory at a time; the
+    rest wait in the pinned slab, so batches mix both kinds."""
+    sets, autos, kinds, machines = fleet
+    rng = np.random.default_rng(63)
+    reqs = requests(rng, kinds, 40, lo=(1 << 20) - 4096, hi=1 << 20)
+    srv = A.ac_serve_create(autos, num_streams=2, max_batch_items=16, max_wait_us=2000,
+                            device_mem_budget=6 << 20)
+    tickets = [A.ac_serve_submit(srv, k, t) for k, t in reqs]
+    got = [A.ac_serve_wait(srv, tk, 120_000) for tk in tickets]
+    A.ac_serve_destroy(srv)
+    for (k, t), (m, c) in zip(reqs, got):
+        wm, wc = machines[k].scan(t)
+        assert np.array_equal(m, wm) and np.array_equal(c, wc)
+
+
+def test_unknown_staging(fleet):
+    sets, autos, kinds, machines = fleet
+    with pytest.raises(A.AcError) as e:
+        A.ac_serve_create(autos, staging=2)
+    assert e.value.code == A.AC_EINVAL
