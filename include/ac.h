@@ -339,15 +339,22 @@ typedef struct {
                                  CTA shape) and replay it as one CUDA graph when the same batch -- same
                                  automata, same text pointers, lengths and formats -- is scanned again; the
                                  first such call autotunes. At most two plans are kept; ac_batch_release
-                                 drops them. */
+                                 drops them. Implies AC_BATCH_ONE_LAUNCH. */
+#define AC_BATCH_ONE_LAUNCH 4u /* lay every text of an alphabet class out in one arena and scan them in one
+                                  persistent launch. Without it (and without AC_BATCH_GRAPH), byte texts
+                                  whose alphabet leaves a byte free are scanned one automaton at a time as
+                                  one text: the automaton's texts laid end to end, each behind a byte outside
+                                  the alphabet (which sends the walk back to the root), through the single-
+                                  text path and its kernel choice; packed texts always take the arena. */
 
 /* Scan ni texts, each against one of na resident automata (all built on the
- * same device), in one persistent launch per alphabet class: the texts are
- * laid out in one device arena of whole chain rows, grouped by automaton, and
- * a tile list assigns (automaton subset, rows) pairs to persistent CTAs
- * (Section III's input- and pattern-focused splits applied to many texts at
- * once). mem = AC_HOST or AC_DEVICE for all item texts; texts are copied
- * into the arena inside the call. outs[i] receives item i's sorted matches
+ * same device): byte texts whose alphabet leaves a byte free, one automaton
+ * at a time as one text (see AC_BATCH_ONE_LAUNCH); otherwise in one
+ * persistent launch per alphabet class: the texts are laid out in one device
+ * arena of whole chain rows, grouped by automaton, and a tile list assigns
+ * (automaton subset, rows) pairs to persistent CTAs (Section III's input- and
+ * pattern-focused splits applied to many texts at once). mem = AC_HOST or
+ * AC_DEVICE for all item texts; texts are copied inside the call. outs[i] receives item i's sorted matches
  * (positions relative to item i's text) and, unless AC_BATCH_NO_COUNTS, its
  * counts (sized by its automaton's pattern count). Synchronous. Errors:
  * AC_EINVAL (NULL, bad automaton index or format, automata on different

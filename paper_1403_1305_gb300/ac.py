@@ -25,7 +25,7 @@ AC_OK, AC_EINVAL, AC_ENOMEM, AC_ERANGE, AC_ECUDA, AC_ETIMEDOUT, AC_EAGAIN, AC_EB
 AC_U8, AC_PACKED2 = 0, 1
 AC_HOST, AC_DEVICE = 0, 1
 AC_PLACE_AUTO, AC_PLACE_SMEM, AC_PLACE_HYBRID, AC_PLACE_GLOBAL, AC_PLACE_OPT, AC_PLACE_HYBRID16 = 0, 1, 2, 3, 4, 5
-AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH = 1, 2
+AC_BATCH_NO_COUNTS, AC_BATCH_GRAPH, AC_BATCH_ONE_LAUNCH = 1, 2, 4
 AC_MACHINE_DFA, AC_MACHINE_PFAC = 0, 1
 AC_KERNEL_AUTO, AC_KERNEL_GENERAL, AC_KERNEL_LEAN, AC_KERNEL_SHORT = 0, 1, 2, 3
 AC_BUILDER_HOST, AC_BUILDER_DEVICE = 0, 1
@@ -206,19 +206,20 @@ def _device_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _result_to_numpy(r: ac_result):
+def _result_to_numpy(r: ac_result, want_counts: bool = True):
+    # plain copies out of the library's arrays (no per-size ctypes array types)
     m = int(r.num_matches)
+    matches = np.empty((m, 2), dtype=np.uint32)
     if m:
-        buf = C.cast(r.matches, C.POINTER(C.c_uint32 * (2 * m))).contents
-        matches = np.frombuffer(buf, dtype=np.uint32).reshape(m, 2).copy()
-    else:
-        matches = np.zeros((0, 2), dtype=np.uint32)
-    P = int(r.num_patterns)
-    if P and r.counts:
-        cb = C.cast(r.counts, C.POINTER(C.c_uint64 * P)).contents
-        counts = np.frombuffer(cb, dtype=np.uint64).copy()
-    else:
-        counts = np.zeros(P, dtype=np.uint64)
+        C.memmove(matches.ctypes.data, r.matches, 8 * m)
+    counts = None
+    if want_counts:
+        P = int(r.num_patterns)
+        if P and r.counts:
+            counts = np.empty(P, dtype=np.uint64)
+            C.memmove(counts.ctypes.data, r.counts, 8 * P)
+        else:
+            counts = np.zeros(P, dtype=np.uint64)
     lib().ac_result_free(C.byref(r))
     return matches, counts
 
@@ -389,11 +390,8 @@ def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=No
     outs = (ac_result * max(1, len(items)))()
     _check(lib().ac_scan_batch(hs, len(automata), arr, len(items), mem, int(flags), _stream_ptr(stream), outs),
            "ac_scan_batch")
-    res = []
-    for i in range(len(items)):
-        m, c = _result_to_numpy(outs[i])
-        res.append((m, None if flags & AC_BATCH_NO_COUNTS else c))
-    return res
+    want = not (flags & AC_BATCH_NO_COUNTS)
+    return [_result_to_numpy(outs[i], want) for i in range(len(items))]
 
 
 def ac_batch_release():

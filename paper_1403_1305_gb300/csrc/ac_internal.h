@@ -214,11 +214,10 @@ int launch_keys_to_matches(const unsigned long long *keys, const unsigned long l
 int key_shift_for(const ac_automaton *a);
 int launch_pad_keys(unsigned long long *keys, const unsigned long long *num, uint64_t cap, cudaStream_t stream);
 int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t stream);
-// single-launch pad + sort + record conversion for at most kSmallSortMax keys
+// single-launch sort + record conversion of the first min(*num, cap) keys, cap at most kSmallSortMax
 constexpr uint64_t kSmallSortMax = 8192;
-int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
-                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
-                      cudaStream_t stream);
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, uint32_t shift,
+                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream);
 int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int begin_bit, int end_bit,
               void *temp, size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted);
 // first key bit a sort of a's keys must look at (stable sorts)

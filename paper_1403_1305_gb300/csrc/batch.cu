@@ -426,6 +426,227 @@ float time_scan(Plan &P, cudaStream_t s) {
     return best;
 }
 
+// ------------------------------------------------------------ texts as one text per automaton
+// Byte texts whose alphabet leaves a byte free are scanned one automaton at a
+// time as one text: the automaton's texts are laid end to end in one device
+// buffer, each starting on a 16-byte boundary behind at least one byte outside
+// the alphabet. That byte sends the walk back to the root (Section II.A: no
+// pattern contains it), so every text is walked exactly as if alone, and the
+// buffer goes through the single-text path (its automatic kernel choice for
+// the buffer's length). The sorted matches split per text by position; a
+// text's counts are the histogram of its matches.
+
+constexpr uint64_t kSegmentMaxBytes = 1ull << 31;  // bytes of texts in one segment (positions stay 32-bit)
+constexpr uint64_t kGatherChunk = 256u << 10;     // bytes one CTA of the gather copies
+
+struct GatherChunk {
+    const uint8_t *src;  // null: fill with the separator byte
+    uint8_t *dst;
+    uint64_t len;
+};
+
+// Device texts into their places in the segment buffers and the separator
+// bytes around them, one chunk per CTA.
+__global__ void gather_kernel(const GatherChunk *__restrict__ chunks, uint8_t sep) {
+    const GatherChunk c = chunks[blockIdx.x];
+    uint8_t *d = c.dst;
+    if (!c.src) {
+        for (uint64_t i = threadIdx.x; i < c.len; i += blockDim.x) d[i] = sep;
+    } else if ((((uintptr_t)c.src | (uintptr_t)d) & 15) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(c.src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(d);
+        const uint64_t n4 = c.len / 16;
+        for (uint64_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+        for (uint64_t i = n4 * 16 + threadIdx.x; i < c.len; i += blockDim.x) d[i] = c.src[i];
+    } else {
+        for (uint64_t i = threadIdx.x; i < c.len; i += blockDim.x) d[i] = c.src[i];
+    }
+}
+
+// The byte of `a`'s symbol map that lies outside its alphabet, or -1.
+int separator_byte(const ac_automaton *a) {
+    for (int b = 0; b < 256; ++b)
+        if (a->sym_of_byte[b] >= a->sigma) return b;
+    return -1;
+}
+
+struct Segment {
+    const ac_automaton *a = nullptr;
+    std::vector<uint32_t> item;   // caller's item indices, in layout order
+    std::vector<uint64_t> off;    // byte offset of each text in the buffer
+    uint64_t len = 0;             // bytes from the buffer start to the last text's end
+    uint64_t alloc = 0;
+    uint8_t *buf = nullptr;
+    unsigned long long *keys = nullptr;
+    uint64_t cap = 0;
+};
+
+int scan_segments(const ac_automaton *const *as, const ac_batch_item *items, const std::vector<uint32_t> &idx,
+                  int mem, uint32_t flags, uint8_t sep, cudaStream_t s, ac_result *outs) {
+    struct Pool {  // stream-ordered scratch, released when the call ends
+        cudaStream_t s;
+        std::vector<void *> ptrs;
+        void *get(size_t bytes) {
+            void *p = dev_alloc(bytes, s);
+            if (p) ptrs.push_back(p);
+            return p;
+        }
+        ~Pool() {
+            for (void *p : ptrs) dev_free(p, s);
+        }
+    } pool{s, {}};
+    // segments: automata in index order, the caller's order within one
+    std::vector<uint32_t> order(idx);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return items[x].automaton < items[y].automaton; });
+    std::vector<Segment> segs;
+    for (uint32_t i : order) {
+        const ac_automaton *a = as[items[i].automaton];
+        const uint64_t n = items[i].n;
+        const uint64_t at = segs.empty() || segs.back().a != a ? 0 : (segs.back().len + 1 + 15) / 16 * 16;
+        if (segs.empty() || segs.back().a != a || at + n > kSegmentMaxBytes) {
+            segs.emplace_back();
+            segs.back().a = a;
+            segs.back().item.push_back(i);
+            segs.back().off.push_back(0);
+            segs.back().len = n;
+        } else {
+            segs.back().item.push_back(i);
+            segs.back().off.push_back(at);
+            segs.back().len = at + n;
+        }
+    }
+    const size_t G = segs.size();
+    // buffers; the texts (host texts copied one by one, device texts by the
+    // gather) and the separator bytes between and after them (the gather)
+    std::vector<GatherChunk> chunks;
+    for (size_t g = 0; g < G; ++g) {
+        Segment &sg = segs[g];
+        sg.alloc = std::max<uint64_t>((sg.len + 15) / 16 * 16, kStageBytes);
+        sg.buf = (uint8_t *)pool.get(sg.alloc);
+        if (!sg.buf) return set_error(AC_ENOMEM, "ac_scan_batch: text buffer of %llu bytes", (unsigned long long)sg.alloc);
+        for (size_t k = 0; k < sg.item.size(); ++k) {
+            const ac_batch_item &it = items[sg.item[k]];
+            if (mem == AC_HOST) {
+                BCK(cudaMemcpyAsync(sg.buf + sg.off[k], it.text, it.n, cudaMemcpyHostToDevice, s),
+                    "ac_scan_batch: text copy");
+            } else {
+                for (uint64_t c0 = 0; c0 < it.n; c0 += kGatherChunk)
+                    chunks.push_back(GatherChunk{it.text + c0, sg.buf + sg.off[k] + c0, std::min(kGatherChunk, it.n - c0)});
+            }
+            const uint64_t end = sg.off[k] + it.n;
+            const uint64_t next = k + 1 < sg.item.size() ? sg.off[k + 1] : sg.alloc;
+            if (next > end) chunks.push_back(GatherChunk{nullptr, sg.buf + end, next - end});
+        }
+    }
+    if (!chunks.empty()) {
+        GatherChunk *d_chunks = (GatherChunk *)pool.get(chunks.size() * sizeof(GatherChunk));
+        if (!d_chunks) return set_error(AC_ENOMEM, "ac_scan_batch: gather list");
+        BCK(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(GatherChunk), cudaMemcpyHostToDevice, s),
+            "ac_scan_batch: gather list");
+        for (uint64_t c0 = 0; c0 < chunks.size(); c0 += 65535) {  // at most 65,535 CTAs a launch here
+            const unsigned grid = (unsigned)std::min<uint64_t>(65535, chunks.size() - c0);
+            gather_kernel<<<grid, 256, 0, s>>>(d_chunks + c0, sep);
+        }
+        BCK(cudaGetLastError(), "ac_scan_batch: gather");
+    }
+    // counters: [2g] matches of segment g, [2g + 1] its error word
+    unsigned long long *d_ctr = (unsigned long long *)pool.get(G * 16);
+    if (!d_ctr) return set_error(AC_ENOMEM, "ac_scan_batch: counters");
+    std::vector<unsigned long long> h_ctr(2 * G);
+    auto scan_all = [&](const std::vector<size_t> &which) -> int {
+        for (size_t g : which) {
+            BCK(cudaMemsetAsync(d_ctr + 2 * g, 0, 16, s), "ac_scan_batch: counters");
+            Segment &sg = segs[g];
+            ac_scan_config cfg;
+            default_config(sg.a, sg.len, AC_U8, &cfg);
+            ScanText t{sg.buf, sg.len, AC_U8, sg.alloc};
+            ScanOut o{sg.keys, sg.cap, d_ctr + 2 * g, nullptr, (uint32_t *)(d_ctr + 2 * g + 1)};
+            const int rc = launch_scan(sg.a, t, o, cfg, s);
+            if (rc) return rc;
+        }
+        BCK(cudaMemcpyAsync(h_ctr.data(), d_ctr, G * 16, cudaMemcpyDeviceToHost, s), "ac_scan_batch: counters");
+        BCK(cudaStreamSynchronize(s), "ac_scan_batch: scan");
+        for (size_t g : which)
+            if ((uint32_t)h_ctr[2 * g + 1]) return set_error(AC_ETIMEDOUT, "ac_scan_batch: a device-side wait ran out");
+        return AC_OK;
+    };
+    std::vector<size_t> all(G);
+    std::iota(all.begin(), all.end(), 0);
+    for (Segment &sg : segs) {
+        sg.cap = std::min<uint64_t>(sg.len / 256 + 4096, 1ull << 26);
+        sg.keys = (unsigned long long *)pool.get(sg.cap * 8);
+        if (!sg.keys) return set_error(AC_ENOMEM, "ac_scan_batch: match keys");
+    }
+    int rc = scan_all(all);
+    if (rc) return rc;
+    std::vector<size_t> over;
+    for (size_t g = 0; g < G; ++g)
+        if (h_ctr[2 * g] > segs[g].cap) {  // more matches than room: scan again with room for all
+            segs[g].cap = h_ctr[2 * g];
+            segs[g].keys = (unsigned long long *)pool.get(segs[g].cap * 8);
+            if (!segs[g].keys) return set_error(AC_ENOMEM, "ac_scan_batch: match keys");
+            over.push_back(g);
+        }
+    if (!over.empty() && (rc = scan_all(over))) return rc;
+    // sort each segment's keys into records, bring them back
+    std::vector<std::vector<ac_match>> rec(G);
+    for (size_t g = 0; g < G; ++g) {
+        Segment &sg = segs[g];
+        const uint64_t M = h_ctr[2 * g];
+        if (!M) continue;
+        ac_match *d_rec = (ac_match *)pool.get(M * sizeof(ac_match));
+        if (!d_rec) return set_error(AC_ENOMEM, "ac_scan_batch: records");
+        const uint32_t shift = (uint32_t)key_shift_for(sg.a);
+        if (M <= kSmallSortMax) {
+            rc = launch_small_sort(sg.keys, d_ctr + 2 * g, M, shift, d_rec, nullptr, nullptr, s);
+        } else {
+            unsigned long long *alt = (unsigned long long *)pool.get(M * 8);
+            if (!alt) return set_error(AC_ENOMEM, "ac_scan_batch: sort buffer");
+            const int end_bit = (int)std::min<uint32_t>(64, shift + value_bits(sg.len ? sg.len - 1 : 0));
+            size_t tb = 0;
+            rc = sort_keys(sg.keys, alt, M, sort_begin_bit(sg.a), end_bit, nullptr, &tb, s, nullptr);
+            void *temp = rc ? nullptr : pool.get(tb);
+            if (!rc && !temp) return set_error(AC_ENOMEM, "ac_scan_batch: sort scratch");
+            unsigned long long *sorted = nullptr;
+            if (!rc) rc = sort_keys(sg.keys, alt, M, sort_begin_bit(sg.a), end_bit, temp, &tb, s, &sorted);
+            if (!rc) rc = launch_keys_to_matches(sorted, d_ctr + 2 * g, M, shift, d_rec, nullptr, nullptr, s);
+        }
+        if (rc) return rc;
+        rec[g].resize(M);
+        BCK(cudaMemcpyAsync(rec[g].data(), d_rec, M * sizeof(ac_match), cudaMemcpyDeviceToHost, s),
+            "ac_scan_batch: records");
+    }
+    BCK(cudaStreamSynchronize(s), "ac_scan_batch: sort");
+    // split per text (records are sorted by position; texts are in position order)
+    const bool counts = !(flags & AC_BATCH_NO_COUNTS);
+    for (size_t g = 0; g < G; ++g) {
+        const Segment &sg = segs[g];
+        size_t r = 0;
+        for (size_t k = 0; k < sg.item.size(); ++k) {
+            ac_result &o = outs[sg.item[k]];
+            o.num_patterns = sg.a->P;
+            const uint64_t lo = sg.off[k], hi = sg.off[k] + items[sg.item[k]].n;
+            while (r < rec[g].size() && rec[g][r].pos < lo) ++r;  // none: separators hold no match
+            size_t e = r;
+            while (e < rec[g].size() && rec[g][e].pos < hi) ++e;
+            o.num_matches = e - r;
+            if (e > r) {
+                o.matches = (ac_match *)malloc((e - r) * sizeof(ac_match));
+                if (!o.matches) return set_error(AC_ENOMEM, "ac_scan_batch: host results");
+                for (size_t q = r; q < e; ++q) o.matches[q - r] = ac_match{(uint32_t)(rec[g][q].pos - lo), rec[g][q].pattern_id};
+            }
+            if (counts) {
+                o.counts = (uint64_t *)calloc(sg.a->P ? sg.a->P : 1, 8);
+                if (!o.counts) return set_error(AC_ENOMEM, "ac_scan_batch: host counts");
+                for (size_t q = r; q < e; ++q) o.counts[rec[g][q].pattern_id]++;
+            }
+            r = e;
+        }
+    }
+    return AC_OK;
+}
+
 }  // namespace
 }  // namespace acgb
 
@@ -497,6 +718,12 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
         const auto &idx = classes[c];
         const ac_automaton *rep = class_rep[c].second;
         const int fmt = class_rep[c].first;
+        // byte texts of an alphabet with a free byte: one text per automaton
+        const int sep = fmt == AC_U8 && !(flags & (AC_BATCH_GRAPH | AC_BATCH_ONE_LAUNCH)) ? separator_byte(rep) : -1;
+        if (sep >= 0) {
+            rc = scan_segments(as, items, idx, mem, flags, (uint8_t)sep, s, outs);
+            continue;
+        }
         uint64_t total = 0;
         uint32_t warm = 0;
         for (uint32_t i : idx) {

@@ -568,8 +568,7 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
         if (M && M <= kSmallSortMax) {
             ac_match *d_m = (ac_match *)sc.get(M * sizeof(ac_match));
             if (!d_m) return set_error(AC_ENOMEM, "ac_scan: records");
-            const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n - 1));
-            e = launch_small_sort(keys, num, M, sort_begin_bit(a), end_bit, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
+            e = launch_small_sort(keys, num, M, (uint32_t)key_shift_for(a), d_m, nullptr, nullptr, s);
             if (e) return e;
             r.matches = (ac_match *)malloc(M * sizeof(ac_match));
             if (!r.matches) return set_error(AC_ENOMEM, "ac_scan: host matches");
@@ -610,6 +609,44 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
 
 int ac_key_shift(const ac_automaton *a) { return a ? key_shift_for(a) : 0; }
 
+// The scan up to unsorted keys. With err_out, the error word (or null when
+// the kernel has no device-side waits) is handed to the caller, who reports
+// it (the sort does); without, a marking kernel writes it into *d_num.
+static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, cudaStream_t s, Scratch &sc,
+                     uint64_t *d_keys, uint64_t cap, uint64_t *d_num, uint64_t *d_counts, const uint32_t **err_out) {
+    int rc;
+    const uint8_t *t = nullptr;
+    uint64_t readable = 0;
+    if (n) {
+        rc = stage_text(d_text, text_bytes(n, fmt), AC_DEVICE, s, sc, &t, &readable);
+        if (rc) return rc;
+    }
+    ac_scan_config cfg{};
+    if (n) default_config(a, n, fmt, &cfg);
+    // the short-text kernel has no device-side waits: no error word to check
+    const bool waits = n && !(a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_SHORT);
+    uint32_t *err = nullptr;
+    if (waits) {
+        err = (uint32_t *)sc.get(16);
+        if (!err) return set_error(AC_ENOMEM, "ac_scan_keys_async: scratch");
+        CK(cudaMemsetAsync(err, 0, 16, s), "ac_scan_keys_async: memset");
+    }
+    CK(cudaMemsetAsync(d_num, 0, 8, s), "ac_scan_keys_async: memset");
+    if (d_counts) CK(cudaMemsetAsync(d_counts, 0, (size_t)a->P * 8, s), "ac_scan_keys_async: memset counts");
+    if (n) {
+        ScanText tx{t, n, fmt, readable};
+        ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
+                  err};
+        rc = launch_scan(a, tx, o, cfg, s);
+        if (rc) return rc;
+    }
+    if (err_out) {
+        *err_out = err;
+        return AC_OK;
+    }
+    return waits ? launch_mark_error((unsigned long long *)d_num, err, s) : AC_OK;
+}
+
 int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
                        uint64_t *d_keys, uint64_t cap, uint64_t *d_num, uint64_t *d_counts) {
     int rc = check_scan_args(a, n, fmt);
@@ -619,43 +656,16 @@ int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n,
     if (!g.ok) return set_error(AC_ECUDA, "ac_scan_keys_async: cannot use device %d", a->device);
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
-    const uint8_t *t = nullptr;
-    uint64_t readable = 0;
-    if (n) {
-        rc = stage_text(d_text, text_bytes(n, fmt), AC_DEVICE, s, sc, &t, &readable);
-        if (rc) return rc;
-    }
-    uint32_t *err = (uint32_t *)sc.get(16);
-    if (!err) return set_error(AC_ENOMEM, "ac_scan_keys_async: scratch");
-    CK(cudaMemsetAsync(err, 0, 16, s), "ac_scan_keys_async: memset");
-    CK(cudaMemsetAsync(d_num, 0, 8, s), "ac_scan_keys_async: memset");
-    if (d_counts) CK(cudaMemsetAsync(d_counts, 0, (size_t)a->P * 8, s), "ac_scan_keys_async: memset counts");
-    if (n) {
-        ac_scan_config cfg;
-        default_config(a, n, fmt, &cfg);
-        ScanText tx{t, n, fmt, readable};
-        ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
-                  err};
-        rc = launch_scan(a, tx, o, cfg, s);
-        if (rc) return rc;
-    }
-    return launch_mark_error((unsigned long long *)d_num, err, s);
+    return scan_keys(a, d_text, n, fmt, s, sc, d_keys, cap, d_num, d_counts, nullptr);
 }
 
-int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
-                       void *stream, ac_match *d_matches, uint64_t *d_num_out) {
-    if (!a || !d_num || (cap && (!d_keys || !d_matches)))
-        return set_error(AC_EINVAL, "ac_sort_keys_async: NULL argument");
-    if (a->device < 0) return set_error(AC_EINVAL, "ac_sort_keys_async: host-only automaton");
-    DeviceGuard g(a->device);
-    if (!g.ok) return set_error(AC_ECUDA, "ac_sort_keys_async: cannot use device %d", a->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cap <= kSmallSortMax) {
-        const int end_bit = (int)std::min<uint32_t>(64, key_shift_for(a) + bits_for(n ? n - 1 : 0));
+// The sort of the keys into records; err (or null): a scan's error word,
+// reported as *d_num_out = UINT64_MAX.
+static int sort_to_matches(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
+                           cudaStream_t s, ac_match *d_matches, uint64_t *d_num_out, const uint32_t *err) {
+    if (cap <= kSmallSortMax)
         return launch_small_sort((const unsigned long long *)d_keys, (const unsigned long long *)d_num, cap,
-                                 sort_begin_bit(a), end_bit,
-                                 (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, nullptr, s);
-    }
+                                 (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, err, s);
     Scratch sc(s);
     const uint64_t kcap = cap ? cap : 1;
     unsigned long long *alt = (unsigned long long *)sc.get(kcap * 8);
@@ -676,7 +686,17 @@ int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, cons
         if (rc) return rc;
     }
     return launch_keys_to_matches(sorted, (const unsigned long long *)d_num, cap, (uint32_t)key_shift_for(a),
-                                  d_matches, (unsigned long long *)d_num_out, nullptr, s);
+                                  d_matches, (unsigned long long *)d_num_out, err, s);
+}
+
+int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
+                       void *stream, ac_match *d_matches, uint64_t *d_num_out) {
+    if (!a || !d_num || (cap && (!d_keys || !d_matches)))
+        return set_error(AC_EINVAL, "ac_sort_keys_async: NULL argument");
+    if (a->device < 0) return set_error(AC_EINVAL, "ac_sort_keys_async: host-only automaton");
+    DeviceGuard g(a->device);
+    if (!g.ok) return set_error(AC_ECUDA, "ac_sort_keys_async: cannot use device %d", a->device);
+    return sort_to_matches(a, n, d_keys, d_num, cap, (cudaStream_t)stream, d_matches, d_num_out, nullptr);
 }
 
 int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
@@ -691,9 +711,11 @@ int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int 
     Scratch sc(s);
     uint64_t *keys = (uint64_t *)sc.get((cap ? cap : 1) * 8);
     if (!keys) return set_error(AC_ENOMEM, "ac_scan_async: scratch");
-    rc = ac_scan_keys_async(a, d_text, n, fmt, stream, keys, cap, d_num_matches, d_counts);
+    // the sort reports the scan's error word (no separate marking launch)
+    const uint32_t *err = nullptr;
+    rc = scan_keys(a, d_text, n, fmt, s, sc, keys, cap, d_num_matches, d_counts, &err);
     if (rc) return rc;
-    return ac_sort_keys_async(a, n, keys, d_num_matches, cap, stream, d_matches, d_num_matches);
+    return sort_to_matches(a, n, keys, d_num_matches, cap, s, d_matches, d_num_matches, err);
 }
 
 }  // extern "C"

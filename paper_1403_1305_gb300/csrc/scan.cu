@@ -2,11 +2,11 @@
 // memory), the small helper kernels (key padding, record conversion, error
 // mark), and the radix sort of the match keys. The scan kernel itself is in
 // scan_kernel.cuh (instantiated by the scan_k_*.cu translation units).
-#include <cub/block/block_radix_sort.cuh>
 #include <cub/device/device_radix_sort.cuh>
 
 #include "scan_kernel.cuh"
 #include "scan_lean.cuh"
+#include "scan_short.cuh"
 
 namespace acgb {
 using namespace kern;
@@ -832,72 +832,102 @@ int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "mark: %s", cudaGetErrorString(e));
 }
 
-// Up to kSmallSortMax keys: one CTA loads the first min(M, cap) keys (the
-// rest as all-ones), radix-sorts them in shared memory and writes the
-// (position, id) records -- pad, sort and conversion in one launch.
+// Up to kSmallSortMax keys, sorted by rank: keys are distinct (one
+// (position, pattern) pair each), so a key's place in the sorted order is the
+// number of keys below it and each key is written straight there -- one
+// launch, no digit passes. A CTA copies all the keys into shared memory
+// (asynchronous 16-byte copies, one round trip) and ranks 32 of them: a thread
+// holds 4 keys and counts the keys below them in one of 64 interleaved slices
+// of the key array (read 16 bytes at once, each read serving 8 comparisons);
+// the slices' counts are summed with shuffles and then across the two warps
+// of a slice group. The records are the (position, id) pairs of the keys.
 namespace {
-// 6-bit digits: the rank counters (64 digits x 1024 threads) still fit in shared memory
-template <int T, int I>
-using SmallSort = cub::BlockRadixSort<unsigned long long, T, I, cub::NullType, 6>;
+constexpr uint32_t kRankKeys = 32, kRankPer = 4, kRankPhases = 64;
+constexpr uint32_t kRankGroups = kRankKeys / kRankPer;        // 8 groups of 4 keys
+constexpr uint32_t kRankThreads = kRankGroups * kRankPhases;  // 512: a group is two warps
 
-template <int T, int I>
-__global__ void __launch_bounds__(T, 1)
-    small_sort_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num, uint64_t cap,
-                      int begin_bit, int end_bit, uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out,
-                      const uint32_t *err) {
-    extern __shared__ __align__(16) unsigned char tmp[];
-    typename SmallSort<T, I>::TempStorage &ts = *reinterpret_cast<typename SmallSort<T, I>::TempStorage *>(tmp);
-    const unsigned long long M = *num;
-    const uint64_t m = M < cap ? M : cap;
-    unsigned long long k[I];
-#pragma unroll
-    for (int i = 0; i < I; ++i) {
-        const uint64_t idx = (uint64_t)threadIdx.x * I + i;
-        k[i] = idx < m ? keys[idx] : ~0ull;
+__global__ void __launch_bounds__(kRankThreads)
+    rank_sort_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num, uint64_t cap,
+                     uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out, const uint32_t *err) {
+    extern __shared__ __align__(16) unsigned long long sk[];  // pairs(cap) * 2 keys
+    __shared__ uint32_t part[kRankGroups][2][kRankPer];      // per group: each warp's counts
+    const unsigned long long M = *num;  // num_out may be num: read before anything is written
+    const bool failed = err && *err;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && num_out) *num_out = failed ? ~0ull : M;
+    const uint32_t m = (uint32_t)(M < cap ? M : cap);
+    const uint32_t kb = blockIdx.x * kRankKeys;
+    if (failed || kb >= m) return;  // uniform across the CTA
+    const uint32_t pairs = (m + 1) / 2;
+    const uint32_t base = smem_addr(sk);
+    // an odd count's last pair is the last key and the all-ones pad (never below a key)
+    if (((uintptr_t)keys & 15) == 0) {
+        for (uint32_t t = threadIdx.x; t < m / 2; t += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16 * t), "l"(keys + 2 * t)
+                         : "memory");
+    } else {  // keys only 8-byte aligned
+        for (uint32_t t = threadIdx.x; t < m / 2 * 2; t += blockDim.x) sk[t] = keys[t];
     }
-    SmallSort<T, I>(ts).Sort(k, begin_bit, end_bit);
-    const unsigned long long mask = (1ull << shift) - 1ull;
+    if ((m & 1) && threadIdx.x == 0) {
+        sk[m - 1] = keys[m - 1];
+        sk[m] = ~0ull;
+    }
+    const uint32_t ph = threadIdx.x % kRankPhases, grp = threadIdx.x / kRankPhases;
+    unsigned long long ki[kRankPer];
 #pragma unroll
-    for (int i = 0; i < I; ++i) {
-        const uint64_t idx = (uint64_t)threadIdx.x * I + i;
-        if (idx < m) {
-            ac_match r;
-            r.pos = (uint32_t)(k[i] >> shift);
-            r.pattern_id = (uint32_t)(k[i] & mask);
-            out[idx] = r;
+    for (uint32_t r = 0; r < kRankPer; ++r) {
+        const uint32_t i = kb + grp * kRankPer + r;
+        ki[r] = i < m ? keys[i] : ~0ull;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const uint4 *sk4 = reinterpret_cast<const uint4 *>(sk);
+    uint32_t below[kRankPer] = {0, 0, 0, 0};
+#pragma unroll 2
+    for (uint32_t j = ph; j < pairs; j += kRankPhases) {
+        const uint4 v = sk4[j];  // keys 2j and 2j + 1
+        const unsigned long long x = ((unsigned long long)v.y << 32) | v.x;
+        const unsigned long long y = ((unsigned long long)v.w << 32) | v.z;
+#pragma unroll
+        for (uint32_t r = 0; r < kRankPer; ++r) below[r] += (x < ki[r] ? 1u : 0u) + (y < ki[r] ? 1u : 0u);
+    }
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (uint32_t r = 0; r < kRankPer; ++r) {
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) below[r] += __shfl_xor_sync(kFull, below[r], o);
+        if (lane == 0) part[grp][(threadIdx.x / 32) & 1][r] = below[r];
+    }
+    __syncthreads();
+    if (threadIdx.x < kRankKeys) {
+        const uint32_t g = threadIdx.x / kRankPer, r = threadIdx.x % kRankPer;
+        const uint32_t i = kb + threadIdx.x;
+        if (i < m) {
+            const unsigned long long k = sk[i];
+            ac_match rec;
+            rec.pos = (uint32_t)(k >> shift);
+            rec.pattern_id = (uint32_t)(k & ((1ull << shift) - 1ull));
+            out[part[g][0][r] + part[g][1][r]] = rec;
         }
     }
-    if (threadIdx.x == 0 && num_out) *num_out = (err && *err) ? ~0ull : M;
-}
-
-// one CTA sized to the capacity (the sort's passes cost in proportion to the items)
-template <int T, int I>
-int small_sort_launch(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
-                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
-                      cudaStream_t stream) {
-    const int smem = (int)sizeof(typename SmallSort<T, I>::TempStorage);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(small_sort_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    });
-    if (attr != cudaSuccess) return set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(attr));
-    small_sort_kernel<T, I><<<1, T, smem, stream>>>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(e));
 }
 }  // namespace
 
-int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, int begin_bit,
-                      int end_bit, uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
-                      cudaStream_t stream) {
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, uint32_t shift,
+                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream) {
     if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
                                               (unsigned long long)kSmallSortMax);
-    if (cap <= 512)
-        return small_sort_launch<128, 4>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
-    if (cap <= 2048)
-        return small_sort_launch<256, 8>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
-    return small_sort_launch<1024, 8>(keys, num, cap, begin_bit, end_bit, shift, out, num_out, err, stream);
+    const int smem = (int)(((cap + 1) / 2 + 1) * 16);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(rank_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((kSmallSortMax / 2 + 1) * 16));
+    });
+    if (attr != cudaSuccess) return set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(attr));
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, (cap + kRankKeys - 1) / kRankKeys);
+    rank_sort_kernel<<<grid, kRankThreads, smem, stream>>>(keys, num, cap, shift, out, num_out, err);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(e));
 }
 
 int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int begin_bit, int end_bit,

@@ -808,15 +808,5 @@ KernelFn kernels_u8_acgt_single_track_r2(int mode, uint32_t bx, uint32_t C);
 KernelFn kernels_packed_single_plain_r2(int mode, uint32_t bx, uint32_t C);
 KernelFn kernels_packed_single_track_r2(int mode, uint32_t bx, uint32_t C);
 
-// ------------------------------------------------------------ short-text kernel (scan_short.cu)
-enum { SHORT_FULL = kShortFull, SHORT_E16 = kShortE16 };
-constexpr uint32_t kShortMaxWords = 9;  // warm-up words + row words a thread holds
-using ShortFn = void (*)(ScanParams);
-// words = warm-up words + row words of a thread's window
-ShortFn short_u8_full(uint32_t words);
-ShortFn short_u8_e16(uint32_t words);
-ShortFn short_packed_full(uint32_t words);
-ShortFn short_packed_e16(uint32_t words);
-
 }  // namespace kern
 }  // namespace acgb

@@ -24,7 +24,7 @@
 // 4-letter alphabet works; a byte outside the alphabet sends the walk to the
 // root (Section II.A: no pattern contains it).
 #include "ac_internal.h"
-#include "scan_kernel.cuh"
+#include "scan_short.cuh"
 
 namespace acgb {
 namespace kern {

@@ -2,7 +2,9 @@
 
 Batches mix automata (several pattern sets, subset counts), alphabets (DNA
 and protein, which go to separate launches), text formats, empty and short
-texts, and memory kinds; the graph-replay plan is checked on repeat calls,
+texts, and memory kinds, through both batch paths (byte texts one
+automaton at a time as one text, separated by a byte outside the alphabet;
+the one-launch arena); the graph-replay plan is checked on repeat calls,
 including after the texts change in place.
 """
 import numpy as np
@@ -56,6 +58,10 @@ def test_mixed_batch_host_and_device():
     dev = [(a, torch.from_numpy(t).cuda() if t.size else torch.zeros(1, dtype=torch.uint8, device="cuda"), n, f)
            for a, t, n, f in items]
     check(A.ac_scan_batch(autos, dev, mem=A.AC_DEVICE), items, sets, texts)
+    # the one-launch arena (texts one automaton at a time as one text is the default for byte texts)
+    check(A.ac_scan_batch(autos, items, flags=A.AC_BATCH_ONE_LAUNCH), items, sets, texts)
+    check(A.ac_scan_batch(autos, dev, mem=A.AC_DEVICE, flags=A.AC_BATCH_ONE_LAUNCH | A.AC_BATCH_NO_COUNTS),
+          items, sets, texts, counts=False)
 
 
 def test_packed_and_protein_classes_in_one_call():
@@ -107,6 +113,36 @@ def test_config4_shape_reduced():
     items = [(int(a), t, t.size, A.AC_U8) for a, t in zip(w.set_of_text, w.texts)]
     res = A.ac_scan_batch(autos, items)
     check(res, items, w.pattern_sets, w.texts)
+    dev = [(a, torch.from_numpy(t).cuda(), n, f) for a, t, n, f in items]
+    check(A.ac_scan_batch(autos, dev, mem=A.AC_DEVICE), items, w.pattern_sets, w.texts)
+    check(A.ac_scan_batch(autos, dev, mem=A.AC_DEVICE, flags=A.AC_BATCH_ONE_LAUNCH), items, w.pattern_sets, w.texts)
+
+
+def test_separator_bytes_inside_texts():
+    """Texts one automaton at a time: bytes outside the alphabet inside the
+    texts, texts that end or start with them, and device texts at odd
+    offsets (not 16-byte aligned) in the gather."""
+    rng = np.random.default_rng(43)
+    clean = [workloads.dna_text(rng, n).copy() for n in (1, 2, 17, 33, 300, 5000, 70_000, 250_001)]
+    sets = make_sets(rng, [t for t in clean if len(t) > 100], [50, 400], 3, 20)
+    texts = []
+    for t in clean:
+        t = t.copy()
+        mask = rng.random(t.size) < 0.02
+        t[mask] = rng.choice(np.frombuffer(b"N\x00xACGT", np.uint8), size=int(mask.sum()))
+        if t.size > 2:
+            t[0], t[-1] = ord("N"), 0
+        texts.append(t)
+    autos = [A.ac_build(sets[0], alphabet="ACGT"), A.ac_build(sets[1], alphabet="ACGT")]
+    items = [(i % 2, t, t.size, A.AC_U8) for i, t in enumerate(texts)]
+    check(A.ac_scan_batch(autos, items), items, sets, texts)
+    big = torch.zeros(sum(t.size + 3 for t in texts) + 64, dtype=torch.uint8, device="cuda")
+    dev, at = [], 5
+    for (a, t, n, f) in items:
+        big[at:at + n] = torch.from_numpy(t).cuda()
+        dev.append((a, big[at:at + n], n, f))
+        at += n + 3
+    check(A.ac_scan_batch(autos, dev, mem=A.AC_DEVICE), items, sets, texts)
 
 
 def test_batch_errors():

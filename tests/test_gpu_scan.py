@@ -242,7 +242,7 @@ def test_failure_less_machine_config3():
 
 
 def test_async_sort_paths():
-    """Capacities at or below the one-CTA sort limit and above it (device radix sort)."""
+    """Capacities at or below the single-launch rank sort's limit (8,192 keys) and above it (device radix sort)."""
     import itertools
     rng = np.random.default_rng(91)
     pats = [bytes(p) for p in itertools.product(b"ACGT", repeat=4)]   # every window matches
@@ -263,6 +263,32 @@ def test_async_sort_paths():
             assert int(d_num.item()) == M
             got = d_m.view(-1, 2)[:M].cpu().numpy().view(np.uint32)
             same((got, d_c.cpu().numpy().view(np.uint64)), want)
+
+
+def test_sort_of_keys_at_an_8_byte_offset():
+    """The rank sort reads keys 16 bytes at a time when it can; a key buffer
+    that starts 8 bytes past a 16-byte boundary takes its plain loads."""
+    import itertools
+    rng = np.random.default_rng(92)
+    pats = [bytes(p) for p in itertools.product(b"ACGT", repeat=4)]
+    a = A.ac_build(pats, alphabet="ACGT")
+    for n in (3001, 6000):
+        text = workloads.dna_text(rng, n)
+        want = oracle.scan(pats, text)
+        M = want[0].shape[0]
+        cap = 8192
+        dt = torch.from_numpy(text).cuda()
+        keys = torch.zeros(cap + 1, dtype=torch.int64, device="cuda")[1:]
+        d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+        d_c = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+        A.ac_scan_keys_async(a, dt, n, A.AC_U8, None, keys, cap, d_num, d_c)
+        d_m = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
+        d_num2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        A.ac_sort_keys_async(a, n, keys, d_num, cap, None, d_m, d_num2)
+        torch.cuda.synchronize()
+        assert int(d_num2.item()) == M
+        got = d_m.view(-1, 2)[:M].cpu().numpy().view(np.uint32)
+        same((got, d_c.cpu().numpy().view(np.uint64)), want)
 
 
 def test_tune_and_table_caps():
