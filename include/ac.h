@@ -370,6 +370,18 @@ AC_API void ac_batch_release(void);
 /* Release the arrays of a result (NULL or zeroed is a no-op). */
 AC_API void ac_result_free(ac_result *r);
 
+/* Move n results into two flat host arrays and release them (as
+ * ac_result_free): matches of outs[i] to matches[moff[i] .. moff[i] +
+ * outs[i].num_matches), where moff[0] = 0 and moff[i + 1] = moff[i] +
+ * outs[i].num_matches (written by the call, n + 1 entries); with counts not
+ * NULL, the counts of outs[i] (num_patterns entries, zeros when outs[i] has
+ * none) to counts[coff[i] ..), coff likewise over num_patterns (n + 1
+ * entries). The caller sizes matches and counts from the results' fields
+ * (sum of num_matches, sum of num_patterns). Host memory only. AC_EINVAL for
+ * NULL arguments (nothing is moved or released then). */
+AC_API int ac_results_take(ac_result *outs, uint32_t n, ac_match *matches, uint64_t *moff, uint64_t *counts,
+                           uint64_t *coff);
+
 /* ------------------------------------------------------------ serving */
 typedef struct {
     uint64_t device_mem_budget; /* bytes of device memory the server may hold for texts and results

@@ -33,7 +33,7 @@ AC_STAGE_DEVICE, AC_STAGE_PINNED = 0, 1
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
-    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_serve_create", "ac_serve_submit",
+    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
     "ac_version",
 )
@@ -127,6 +127,7 @@ def _declare(lib):
                                     C.POINTER(ac_result)]),
         "ac_batch_release": (None, []),
         "ac_result_free": (None, [C.POINTER(ac_result)]),
+        "ac_results_take": (C.c_int, [C.POINTER(ac_result), u32, vp, vp, vp, vp]),
         "ac_serve_create": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_serve_opts), C.POINTER(vp)]),
         "ac_serve_submit": (C.c_int, [vp, u32, vp, u64, C.c_int, C.POINTER(u64)]),
         "ac_serve_poll": (C.c_int, [vp, u64, C.POINTER(ac_result)]),
@@ -222,6 +223,36 @@ def _result_to_numpy(r: ac_result, want_counts: bool = True):
             counts = np.zeros(P, dtype=np.uint64)
     lib().ac_result_free(C.byref(r))
     return matches, counts
+
+
+# numpy view of an ac_result array (field offsets from the ctypes layout)
+_RESULT_DTYPE = np.dtype({"names": ["num_matches", "num_patterns"], "formats": [np.uint64, np.uint32],
+                          "offsets": [ac_result.num_matches.offset, ac_result.num_patterns.offset],
+                          "itemsize": C.sizeof(ac_result)})
+
+
+def _take_results(outs, n: int, want_counts: bool = True):
+    """Results outs[0..n) as ``(matches, counts)`` pairs: one copy out of the
+    library into two flat arrays (ac_results_take, which releases the
+    results), each pair views into them; counts None unless want_counts."""
+    if n == 0:
+        return []
+    rec = np.frombuffer(outs, dtype=_RESULT_DTYPE, count=n)
+    matches = np.empty((int(rec["num_matches"].sum()), 2), dtype=np.uint32)
+    moff = np.empty(n + 1, dtype=np.uint64)
+    counts = coff = None
+    if want_counts:
+        counts = np.empty(int(rec["num_patterns"].astype(np.uint64).sum()), dtype=np.uint64)
+        coff = np.empty(n + 1, dtype=np.uint64)
+    _check(lib().ac_results_take(outs, n, matches.ctypes.data, moff.ctypes.data,
+                                 counts.ctypes.data if want_counts else None,
+                                 coff.ctypes.data if want_counts else None), "ac_results_take")
+    mo = moff.tolist()
+    ms = [matches[mo[i]:mo[i + 1]] for i in range(n)]
+    if not want_counts:
+        return [(m, None) for m in ms]
+    co = coff.tolist()
+    return [(ms[i], counts[co[i]:co[i + 1]]) for i in range(n)]
 
 
 # ---------------------------------------------------------------- automaton
@@ -390,8 +421,7 @@ def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=No
     outs = (ac_result * max(1, len(items)))()
     _check(lib().ac_scan_batch(hs, len(automata), arr, len(items), mem, int(flags), _stream_ptr(stream), outs),
            "ac_scan_batch")
-    want = not (flags & AC_BATCH_NO_COUNTS)
-    return [_result_to_numpy(outs[i], want) for i in range(len(items))]
+    return _take_results(outs, len(items), not (flags & AC_BATCH_NO_COUNTS))
 
 
 def ac_batch_release():

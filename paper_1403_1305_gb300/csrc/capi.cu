@@ -488,6 +488,38 @@ void ac_result_free(ac_result *r) {
     memset(r, 0, sizeof(*r));
 }
 
+int ac_results_take(ac_result *outs, uint32_t n, ac_match *matches, uint64_t *moff, uint64_t *counts,
+                    uint64_t *coff) {
+    if (n && (!outs || !moff)) return set_error(AC_EINVAL, "ac_results_take: NULL argument");
+    if (counts && !coff) return set_error(AC_EINVAL, "ac_results_take: NULL argument");
+    uint64_t mtot = 0;
+    for (uint32_t i = 0; i < n; ++i) mtot += outs[i].num_matches;
+    if (mtot && !matches) return set_error(AC_EINVAL, "ac_results_take: NULL argument");
+    uint64_t m = 0, c = 0;
+    if (n == 0) {
+        if (moff) moff[0] = 0;
+        if (coff) coff[0] = 0;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        ac_result &r = outs[i];
+        moff[i] = m;
+        if (r.num_matches) memcpy(matches + m, r.matches, r.num_matches * sizeof(ac_match));
+        m += r.num_matches;
+        if (counts) {
+            coff[i] = c;
+            if (r.counts) memcpy(counts + c, r.counts, (size_t)r.num_patterns * 8);
+            else memset(counts + c, 0, (size_t)r.num_patterns * 8);
+            c += r.num_patterns;
+        }
+        ac_result_free(&r);
+    }
+    if (n) {
+        moff[n] = m;
+        if (counts) coff[n] = c;
+    }
+    return AC_OK;
+}
+
 int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int mem, void *stream,
             ac_result *out) {
     if (!out) return set_error(AC_EINVAL, "ac_scan: out is NULL");

@@ -337,3 +337,44 @@ def test_escape_coded_prefix():
                               oracle.scan(pats, text[:20_000] if hot < r else text)[0])
     assert want.shape[0] > 0
     assert A.ac_subset(A.ac_build([b"ab", b"ba"], device=-1), 0)["table_e16"] is None
+
+
+def test_results_take_moves_results_into_flat_arrays():
+    """ac_results_take (host only): the matches and counts of several results
+    land in two flat arrays at the offsets it reports, and the results are
+    released (zeroed)."""
+    import ctypes as C
+    libc = C.CDLL(None)
+    libc.malloc.restype = C.c_void_p
+    libc.malloc.argtypes = [C.c_size_t]
+    rng = np.random.default_rng(5)
+    shapes = [(3, 4, True), (0, 2, False), (5, 0, False), (0, 0, False), (7, 3, True)]
+    outs = (A.ac_result * len(shapes))()
+    want_m, want_c = [], []
+    for i, (m, P, with_counts) in enumerate(shapes):
+        mm = rng.integers(0, 1 << 31, size=(m, 2)).astype(np.uint32)
+        cc = rng.integers(0, 1000, size=P).astype(np.uint64) if with_counts else np.zeros(P, np.uint64)
+        want_m.append(mm)
+        want_c.append(cc)
+        if m:
+            p = libc.malloc(8 * m)
+            C.memmove(p, mm.ctypes.data, 8 * m)
+            outs[i].matches = C.cast(p, C.POINTER(A.ac_match))
+        outs[i].num_matches = m
+        if with_counts:
+            q = libc.malloc(8 * P)
+            C.memmove(q, cc.ctypes.data, 8 * P)
+            outs[i].counts = C.cast(q, C.POINTER(C.c_uint64))
+        outs[i].num_patterns = P
+    got = A._take_results(outs, len(shapes), True)
+    for (gm, gc), wm, wc in zip(got, want_m, want_c):
+        assert np.array_equal(gm, wm) and gm.shape == wm.shape
+        assert np.array_equal(gc, wc)
+    for i in range(len(shapes)):
+        assert outs[i].num_matches == 0 and not outs[i].matches and not outs[i].counts
+    # without counts; and the NULL-argument refusal
+    outs2 = (A.ac_result * 1)()
+    outs2[0].num_patterns = 9
+    [(m, c)] = A._take_results(outs2, 1, False)
+    assert m.shape == (0, 2) and c is None
+    assert A.lib().ac_results_take(None, 1, None, None, None, None) == A.AC_EINVAL
