@@ -193,10 +193,11 @@ typedef struct {
 
 /* Scan configuration (ac_set_scan_config / ac_tune). Zero fields = defaults. */
 typedef struct {
-    uint32_t row_len;     /* text symbols per chain (rounded up to 32 bytes of text) */
+    uint32_t row_len;     /* text symbols per chain (rounded up to 32 bytes of text; to 16 bytes, at most 64,
+                             for the short-text kernel) */
     uint32_t threads;     /* threads per CTA (multiple of 32; <= 512 for the general kernel; 512, 768 or
-                             1024 for the lean one) */
-    uint32_t chains;      /* independent chains per thread: 1, 2 or 4 */
+                             1024 for the lean one; 64 to 1024 for the short-text one) */
+    uint32_t chains;      /* independent chains per thread: 1, 2 or 4 (1 for the short-text kernel) */
     uint32_t ctas;        /* persistent grid size; 0 = one per SM */
     uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains; the
                              lean kernel always uses 16) */
