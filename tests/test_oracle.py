@@ -7,7 +7,8 @@ The oracle is checked against things other than itself:
     small cases, and the failure-less walk of Section II.B on the same cases,
   * a closed form: all k-mers as the pattern set match every window, so the
     counts are the k-mer histogram (computed here with numpy, not the oracle),
-  * the input-focused chunked scan (Section III) equals the whole scan,
+  * the input-focused chunked scan (Section III) equals the whole scan, and
+    texts joined by bytes outside the alphabet scan as each text alone,
   * planted mistakes: compiling ``ac_oracle.c`` with ``-DORACLE_MUTANT=k``
     gives variants with a plausible bug each, and every one of them must fail
     at least one of the pins above.
@@ -191,6 +192,34 @@ def test_chunked_threads_equal_whole_scan():
         want = m.scan(text)[0]
         for t in (1, 2, 3, 7, 64):
             assert np.array_equal(m.scan_mt(text, t)[0], want), (i, t)
+
+
+def test_texts_joined_by_a_byte_outside_the_alphabet():
+    """The property one-text-per-automaton batches rest on (Section II.A: no
+    pattern holds a byte outside the alphabet, so the walk returns to the
+    root there): texts joined by one or more such bytes give exactly each
+    text's own matches, shifted by the text's offset, and nothing else."""
+    lib = oracle.load()
+    rng = np.random.default_rng(8)
+    for i in range(100):
+        n_texts = int(rng.integers(1, 6))
+        texts, pats = [], None
+        for _ in range(n_texts):
+            t, p = workloads.tiny_case(rng, b"ACGT", max_n=120, max_p=10, max_len=8)
+            texts.append(t)
+            pats = p if pats is None else pats + p
+        m = oracle.Machine(pats, True, lib)
+        joined, offs = [], []
+        for t in texts:
+            if joined:
+                joined.append(np.full(int(rng.integers(1, 17)), ord("N") if i % 2 else 0, np.uint8))
+            offs.append(sum(x.size for x in joined))
+            joined.append(t)
+        whole = np.concatenate(joined) if joined else np.zeros(0, np.uint8)
+        got = m.scan(whole)[0]
+        want = [np.asarray(m.scan(t)[0], np.int64) + np.array([o, 0]) for t, o in zip(texts, offs)]
+        want = np.concatenate(want) if want else np.zeros((0, 2), np.int64)
+        assert np.array_equal(np.asarray(got, np.int64), want), i
 
 
 def test_edge_cases():
