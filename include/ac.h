@@ -22,6 +22,11 @@
  *  - Return value: AC_OK (0) or a negative AC_E* code; on error no output is
  *    produced (result structs are left zeroed) and ac_last_error() returns a
  *    one-line description for the calling thread.
+ *  - Diagnostics: the environment variable AC_LOG (read once) set to 1
+ *    prints every error message on stderr; 2 also prints one line per build
+ *    (patterns, subsets, states, times), per scan plan (kernel, row length,
+ *    CTA shape) and per batch path. The library marks its host phases with
+ *    NVTX ranges (build, scan, sort, copies) for profilers that record them.
  *  - Pointers marked "device" are CUDA device pointers on the automaton's
  *    device; "host" pointers are ordinary (pageable or pinned) host memory.
  *  - Inputs are borrowed for the duration of the call only (asynchronous

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -119,8 +120,18 @@ int build_subset_device(const uint8_t *const *pats, const uint32_t *lens, uint32
 // symbols per lookup a scan of this format uses under configuration stride `want` (0 = automatic)
 uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want);
 
-// error reporting (capi.cu)
+// A named NVTX range over a host phase (a no-op unless a profiler records NVTX).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// error reporting and the AC_LOG diagnostics (capi.cu)
 int set_error(int code, const char *fmt, ...);
+int log_level();
+void ac_log(int level, const char *fmt, ...);
 
 // scan.cu
 struct ScanText {

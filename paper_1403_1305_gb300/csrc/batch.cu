@@ -654,6 +654,7 @@ using namespace acgb;
 
 extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const ac_batch_item *items, uint32_t ni,
                              int mem, uint32_t flags, void *stream, ac_result *outs) {
+    NvtxRange nvtx_range("ac_scan_batch");
     if (!as || !na || (!items && ni) || (!outs && ni)) return set_error(AC_EINVAL, "ac_scan_batch: NULL argument");
     if (mem != AC_HOST && mem != AC_DEVICE) return set_error(AC_EINVAL, "ac_scan_batch: unknown memory kind");
     for (uint32_t i = 0; i < ni; ++i) memset(&outs[i], 0, sizeof(ac_result));
@@ -720,6 +721,8 @@ extern "C" int ac_scan_batch(const ac_automaton *const *as, uint32_t na, const a
         const int fmt = class_rep[c].first;
         // byte texts of an alphabet with a free byte: one text per automaton
         const int sep = fmt == AC_U8 && !(flags & (AC_BATCH_GRAPH | AC_BATCH_ONE_LAUNCH)) ? separator_byte(rep) : -1;
+        ac_log(2, "batch: %zu texts (%s), %s", idx.size(), fmt == AC_U8 ? "u8" : "packed",
+               sep >= 0 ? "one text per automaton behind separator bytes" : "one-launch arena");
         if (sep >= 0) {
             rc = scan_segments(as, items, idx, mem, flags, (uint8_t)sep, s, outs);
             continue;

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <chrono>
+#include <mutex>
 
 #include "ac_internal.h"
 
@@ -13,11 +14,34 @@ namespace acgb {
 // ------------------------------------------------------------------ errors
 static thread_local char g_last_error[512] = "";
 
+// AC_LOG (environment, read once): 0 or unset = silent, 1 = every error
+// message on stderr, 2 = also one line per build, scan plan and batch path.
+int log_level() {
+    static std::once_flag once;
+    static int level = 0;
+    std::call_once(once, [] {
+        const char *v = getenv("AC_LOG");
+        level = v ? atoi(v) : 0;
+    });
+    return level;
+}
+
+void ac_log(int level, const char *fmt, ...) {
+    if (log_level() < level) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "acgb300: %s\n", buf);
+}
+
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
     va_end(ap);
+    if (log_level() >= 1) fprintf(stderr, "acgb300: error %d: %s\n", code, g_last_error);
     return code;
 }
 
@@ -27,6 +51,14 @@ static int cuda_fail(cudaError_t e, const char *what) {
         return set_error(AC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
     }
     return set_error(AC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static void log_plan(const ac_automaton *a, uint64_t n, int fmt, const ac_scan_config &c) {
+    if (log_level() < 2) return;
+    static const char *kName[4] = {"auto", "general", "lean", "short"};
+    ac_log(2, "scan: %llu symbols (%s) on %u subsets: %s kernel, rows of %u symbols, %u threads x %u chains",
+           (unsigned long long)n, fmt == AC_U8 ? "u8" : "packed", a->K, kName[c.kernel & 3], c.row_len, c.threads,
+           c.chains);
 }
 
 #define CK(call, what)                                   \
@@ -329,6 +361,7 @@ const char *ac_last_error(void) { return g_last_error; }
 
 int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const ac_build_opts *opts,
              ac_automaton **out) {
+    NvtxRange nvtx_range("ac_build");
     if (!out) return set_error(AC_EINVAL, "ac_build: out is NULL");
     *out = nullptr;
     ac_automaton *a = nullptr;
@@ -380,6 +413,12 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
         free_device(a);
         delete a;
         return rc;
+    }
+    if (log_level() >= 2) {
+        uint64_t states = 0;
+        for (auto &sb : a->subs) states += sb.states;
+        ac_log(2, "build: %u patterns, %u subsets, alphabet of %u, %llu states, %.2f ms build, %.2f ms upload",
+               a->P, a->K, a->sigma, (unsigned long long)states, a->build_ms, a->upload_ms);
     }
     *out = a;
     return AC_OK;
@@ -522,6 +561,7 @@ int ac_results_take(ac_result *outs, uint32_t n, ac_match *matches, uint64_t *mo
 
 int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int mem, void *stream,
             ac_result *out) {
+    NvtxRange nvtx_range("ac_scan");
     if (!out) return set_error(AC_EINVAL, "ac_scan: out is NULL");
     memset(out, 0, sizeof(*out));
     int rc = check_scan_args(a, n, fmt);
@@ -574,6 +614,7 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             const uint64_t rb = std::max<uint64_t>(128, 2 * ((warm + 31) / 32 * 32));
             cfg.row_len = (uint32_t)std::min<uint64_t>(rb * (fmt == AC_U8 ? 1 : 4), 1u << 20);
         }
+        log_plan(a, n, fmt, cfg);
         unsigned long long h_num[2];
         unsigned long long *keys = nullptr;
         for (int attempt = 0; attempt < 2; ++attempt) {
@@ -654,7 +695,10 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
         if (rc) return rc;
     }
     ac_scan_config cfg{};
-    if (n) default_config(a, n, fmt, &cfg);
+    if (n) {
+        default_config(a, n, fmt, &cfg);
+        log_plan(a, n, fmt, cfg);
+    }
     // the short-text kernel has no device-side waits: no error word to check
     const bool waits = n && !(a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_SHORT);
     uint32_t *err = nullptr;
@@ -681,6 +725,7 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
 
 int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
                        uint64_t *d_keys, uint64_t cap, uint64_t *d_num, uint64_t *d_counts) {
+    NvtxRange nvtx_range("ac_scan_keys_async");
     int rc = check_scan_args(a, n, fmt);
     if (rc) return rc;
     if ((!d_text && n) || !d_num || (!d_keys && cap)) return set_error(AC_EINVAL, "ac_scan_keys_async: NULL argument");
@@ -723,6 +768,7 @@ static int sort_to_matches(const ac_automaton *a, uint64_t n, uint64_t *d_keys, 
 
 int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
                        void *stream, ac_match *d_matches, uint64_t *d_num_out) {
+    NvtxRange nvtx_range("ac_sort_keys_async");
     if (!a || !d_num || (cap && (!d_keys || !d_matches)))
         return set_error(AC_EINVAL, "ac_sort_keys_async: NULL argument");
     if (a->device < 0) return set_error(AC_EINVAL, "ac_sort_keys_async: host-only automaton");
@@ -733,6 +779,7 @@ int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_keys, cons
 
 int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
                   ac_match *d_matches, uint64_t cap, uint64_t *d_num_matches, uint64_t *d_counts) {
+    NvtxRange nvtx_range("ac_scan_async");
     int rc = check_scan_args(a, n, fmt);
     if (rc) return rc;
     if ((!d_text && n) || !d_num_matches || (!d_matches && cap))

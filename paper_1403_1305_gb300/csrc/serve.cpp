@@ -154,6 +154,7 @@ void worker_loop(ac_server *s, int w) {
             s->items_launched += batch.size();
         }
         if (batch.empty()) continue;
+        acgb::NvtxRange nvtx_range("ac_serve batch");
         // one launch per staging kind: device-staged texts, then host ones
         std::vector<ac_result> outs(batch.size());
         std::vector<int> rcs(batch.size(), AC_OK);
@@ -279,6 +280,7 @@ int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_o
 }
 
 int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt, uint64_t *ticket) {
+    acgb::NvtxRange nvtx_range("ac_serve_submit");
     if (!s || !ticket || (!text && n)) return set_error(AC_EINVAL, "ac_serve_submit: NULL argument");
     if (automaton >= s->as.size()) return set_error(AC_EINVAL, "ac_serve_submit: no automaton %u", automaton);
     if (fmt != AC_U8 && fmt != AC_PACKED2) return set_error(AC_EINVAL, "ac_serve_submit: unknown format");

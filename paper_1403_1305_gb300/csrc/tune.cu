@@ -7,6 +7,7 @@ using namespace acgb;
 
 extern "C" int ac_tune(ac_automaton *a, const uint8_t *d_text, uint64_t n, int fmt, void *stream,
                        ac_scan_config *chosen) {
+    NvtxRange nvtx_range("ac_tune");
     if (!a || (!d_text && n)) return set_error(AC_EINVAL, "ac_tune: NULL argument");
     if (a->device < 0) return set_error(AC_EINVAL, "ac_tune: host-only automaton");
     if (fmt != AC_U8 && fmt != AC_PACKED2) return set_error(AC_EINVAL, "ac_tune: unknown format");

@@ -378,3 +378,31 @@ def test_results_take_moves_results_into_flat_arrays():
     [(m, c)] = A._take_results(outs2, 1, False)
     assert m.shape == (0, 2) and c is None
     assert A.lib().ac_results_take(None, 1, None, None, None, None) == A.AC_EINVAL
+
+
+def test_ac_log_levels():
+    """AC_LOG=2 prints the build line and errors on stderr, AC_LOG=1 errors
+    only, unset nothing (host-only automata: no GPU needed)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1403_1305_gb300 import ac as A\n"
+            "A.ac_build([b'AC', b'GT'], alphabet='ACGT', device=-1)\n"
+            "try:\n"
+            "    A.ac_build([b'AX'], alphabet='ACGT', device=-1)\n"
+            "except A.AcError:\n"
+            "    pass\n") % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    def run(level):
+        env = dict(os.environ)
+        env.pop("AC_LOG", None)
+        if level is not None:
+            env["AC_LOG"] = str(level)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        return [l for l in r.stderr.splitlines() if l.startswith("acgb300:")]
+    two = run(2)
+    assert any("build: 2 patterns" in l for l in two)
+    assert any("error -1" in l and "outside the alphabet" in l for l in two)
+    one = run(1)
+    assert one and all("error" in l for l in one)
+    assert run(None) == []
