@@ -253,6 +253,23 @@ AC_API int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P
 /* Release an automaton (NULL is a no-op). */
 AC_API void ac_free(ac_automaton *a);
 
+/* Write automaton a (its machines, alphabet and build options; not its scan
+ * configuration, nothing device-side) to the file at path, in this library's
+ * own format (host byte order, versioned), so that ac_load can skip the
+ * build. Errors: AC_EINVAL (NULL, the file cannot be written; ac_last_error
+ * says which). */
+AC_API int ac_save(const ac_automaton *a, const char *path);
+
+/* Read an automaton written by ac_save and copy its tables to device
+ * `device` (-1: host only, as ac_build with device -1). The file is checked
+ * before anything reaches a kernel: format and version, sizes, every
+ * transition, failure link, prefix entry and output id inside its machine;
+ * a loaded automaton scans exactly as the saved one, with the default scan
+ * configuration. Errors: AC_EINVAL (NULL, not such a file, truncated,
+ * inconsistent), AC_ERANGE (placement SMEM and a table that does not fit the
+ * device), AC_ENOMEM, AC_ECUDA. */
+AC_API int ac_load(const char *path, int device, ac_automaton **out);
+
 AC_API int ac_stats(const ac_automaton *a, ac_stats_t *out);
 
 /* Host view of subset k (0 <= k < K). */

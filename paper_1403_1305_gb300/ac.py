@@ -32,7 +32,7 @@ AC_BUILDER_HOST, AC_BUILDER_DEVICE = 0, 1
 AC_STAGE_DEVICE, AC_STAGE_PINNED = 0, 1
 
 EXPORTED = (
-    "ac_build", "ac_free", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
+    "ac_build", "ac_free", "ac_save", "ac_load", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
     "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
     "ac_version",
@@ -112,6 +112,8 @@ def _declare(lib):
         "ac_build": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(u32), u32, C.POINTER(ac_build_opts),
                                C.POINTER(vp)]),
         "ac_free": (None, [vp]),
+        "ac_save": (C.c_int, [vp, C.c_char_p]),
+        "ac_load": (C.c_int, [C.c_char_p, C.c_int32, C.POINTER(vp)]),
         "ac_stats": (C.c_int, [vp, C.POINTER(ac_stats_t)]),
         "ac_subset": (C.c_int, [vp, u32, C.POINTER(ac_subset_view)]),
         "ac_set_scan_config": (C.c_int, [vp, C.POINTER(ac_scan_config)]),
@@ -302,6 +304,18 @@ def ac_free(a: Automaton):
     if a is not None and a.h:
         lib().ac_free(a.h)
         a.h = None
+
+
+def ac_save(a: Automaton, path) -> None:
+    _check(lib().ac_save(a.h, os.fsencode(path)), "ac_save")
+
+
+def ac_load(path, device: int = 0) -> Automaton:
+    h = C.c_void_p()
+    _check(lib().ac_load(os.fsencode(path), device, C.byref(h)), "ac_load")
+    st = ac_stats_t()
+    _check(lib().ac_stats(h, C.byref(st)), "ac_stats")
+    return Automaton(h, int(st.num_patterns), device)
 
 
 def ac_stats(a: Automaton) -> dict:

@@ -220,6 +220,24 @@ static int upload(ac_automaton *a) {
     return AC_OK;
 }
 
+// Placement SMEM: every table must fit the general kernel's shared-memory
+// room (the lean kernel steps aside when its own is smaller).
+static int check_smem_placement(ac_automaton *a) {
+    if (a->placement != AC_PLACE_SMEM) return AC_OK;
+    ac_scan_config c{};
+    const ac_scan_config user = a->cfg;
+    a->cfg.kernel = AC_KERNEL_GENERAL;
+    default_config(a, 1, AC_U8, &c);
+    a->cfg = user;
+    int limit = scan_smem_limit(a->device);
+    uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
+    if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
+    for (auto &s : a->subs)
+        if ((uint64_t)s.states * 4 * a->sigma > avail)
+            return set_error(AC_ERANGE, "placement SMEM, but a table of %u states does not fit", s.states);
+    return AC_OK;
+}
+
 static uint32_t bits_for(uint64_t x) {
     uint32_t b = 1;
     while (b < 64 && (x >> b)) ++b;
@@ -393,21 +411,7 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
             if (s.states >= (1u << 30)) rc = set_error(AC_ERANGE, "ac_build: 2^30 states or more");
     if (rc == AC_OK && a->device >= 0) {
         rc = upload(a);
-        if (rc == AC_OK && a->placement == AC_PLACE_SMEM) {
-            // the general kernel's room (the lean kernel steps aside when its own is smaller)
-            ac_scan_config c{};
-            const ac_scan_config user = a->cfg;
-            a->cfg.kernel = AC_KERNEL_GENERAL;
-            default_config(a, 1, AC_U8, &c);
-            a->cfg = user;
-            int limit = scan_smem_limit(a->device);
-            uint64_t avail = (uint64_t)std::max(0, limit - (int)scan_stage_bytes_per_cta(c) - 64);
-            if (a->smem_cap_bytes && a->smem_cap_bytes < avail) avail = a->smem_cap_bytes;
-            for (auto &s : a->subs)
-                if ((uint64_t)s.states * 4 * a->sigma > avail)
-                    rc = set_error(AC_ERANGE, "ac_build: placement SMEM, but a table of %u states does not fit",
-                                   s.states);
-        }
+        if (rc == AC_OK) rc = check_smem_placement(a);
     }
     if (rc != AC_OK) {
         free_device(a);
@@ -428,6 +432,233 @@ void ac_free(ac_automaton *a) {
     if (!a) return;
     free_device(a);
     delete a;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ save / load
+// File layout (host byte order; written and read by this library only):
+// magic, format version, the automaton's fields, then per subset its
+// scalars and its tables, each table as a 64-bit element count followed by
+// the elements. The scan configuration is not kept (a loaded automaton starts
+// at the defaults); nothing device-side is written.
+namespace {
+constexpr char kFileMagic[8] = {'A', 'C', 'G', 'B', '3', '0', '0', 'M'};
+constexpr uint32_t kFileFormat = 1;
+
+struct FileWriter {
+    FILE *f;
+    bool ok = true;
+    template <class T>
+    void put(const T &v) {
+        ok = ok && fwrite(&v, sizeof(T), 1, f) == 1;
+    }
+    template <class T>
+    void vec(const std::vector<T> &v) {
+        const uint64_t n = v.size();
+        put(n);
+        if (n) ok = ok && fwrite(v.data(), sizeof(T), n, f) == n;
+    }
+};
+
+struct FileReader {
+    FILE *f;
+    uint64_t left;  // bytes not yet read: bounds every count taken from the file
+    bool ok = true;
+    template <class T>
+    void get(T &v) {
+        ok = ok && left >= sizeof(T) && fread(&v, sizeof(T), 1, f) == 1;
+        if (ok) left -= sizeof(T);
+    }
+    template <class T>
+    void vec(std::vector<T> &v) {
+        uint64_t n = 0;
+        get(n);
+        if (!ok || n > left / sizeof(T)) {
+            ok = false;
+            return;
+        }
+        v.resize(n);
+        if (n) ok = fread(v.data(), sizeof(T), n, f) == n;
+        if (ok) left -= n * sizeof(T);
+    }
+};
+
+// Every index a scan would follow stays inside its table: a file that fails
+// these checks is refused rather than handed to the kernels.
+const char *check_loaded(const ac_automaton *a) {
+    if (a->sigma == 0 || a->sigma > 255 || a->K == 0 || a->K > a->P || a->subs.size() != a->K)
+        return "bad alphabet size or subset count";
+    if (a->machine != AC_MACHINE_DFA && a->machine != AC_MACHINE_PFAC) return "unknown machine";
+    for (int b = 0; b < 256; ++b)
+        if (a->sym_of_byte[b] > a->sigma) return "bad symbol map";
+    uint32_t next_id = 0, max_len = 0;
+    for (const HostSubset &h : a->subs) {
+        const uint64_t S = h.states;
+        if (S == 0 || S >= (1u << 30)) return "bad state count";
+        if (h.id_lo != next_id || h.id_hi <= h.id_lo || h.id_hi > a->P) return "bad pattern id ranges";
+        next_id = h.id_hi;
+        max_len = std::max(max_len, h.max_len);
+        if (h.table.size() != S * a->sigma || h.out_off.size() != S + 1) return "table sizes disagree";
+        if ((!h.fail.empty() && h.fail.size() != S) || (!h.depth.empty() && h.depth.size() != S))
+            return "table sizes disagree";
+        const bool pfac = a->machine == AC_MACHINE_PFAC;
+        for (uint32_t e : h.table)
+            if ((e & kStateMask) >= S && !(pfac && e == kMissing)) return "a transition leaves the machine";
+        for (uint32_t f : h.fail)
+            if (f >= S) return "a failure link leaves the machine";
+        if (h.out_off[0] != 0 || h.out_off[S] != h.out_ids.size()) return "bad output offsets";
+        for (uint64_t s = 0; s < S; ++s)
+            if (h.out_off[s] > h.out_off[s + 1]) return "bad output offsets";
+        for (uint32_t id : h.out_ids)
+            if (id < h.id_lo || id >= h.id_hi) return "an output id outside the subset";
+        if (!h.table2.empty()) {
+            if (a->sigma != 4 || h.table2.size() != S * 16) return "bad two-symbol table";
+            for (uint32_t e : h.table2)
+                if ((e & kStateMask2) >= S) return "bad two-symbol table";
+        }
+        if (h.table16.size() != (uint64_t)h.rows16 * 4 || h.rows16 > S) return "bad 16-bit prefix";
+        for (uint16_t e : h.table16)
+            if ((uint64_t)(e >> 1) >= S) return "bad 16-bit prefix";
+        if (h.table_e16.size() != (uint64_t)h.rows_e16 * 4 || h.rows_e16 > S) return "bad escape-coded prefix";
+        for (uint16_t e : h.table_e16)
+            if (e != kEsc16 && e >= S) return "bad escape-coded prefix";
+        if ((!h.table16.empty() || !h.table_e16.empty()) && a->sigma != 4) return "16-bit prefix for a 4-letter machine only";
+    }
+    if (next_id != a->P || max_len != a->max_len) return "pattern ids or lengths disagree";
+    return nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+int ac_save(const ac_automaton *a, const char *path) {
+    if (!a || !path) return set_error(AC_EINVAL, "ac_save: NULL argument");
+    FILE *f = fopen(path, "wb");
+    if (!f) return set_error(AC_EINVAL, "ac_save: cannot open %s for writing", path);
+    FileWriter w{f};
+    for (char c : kFileMagic) w.put(c);
+    w.put(kFileFormat);
+    w.put(a->P);
+    w.put(a->K);
+    w.put(a->sigma);
+    w.put(a->max_len);
+    w.put(a->placement);
+    w.put(a->machine);
+    w.put(a->smem_cap_bytes);
+    w.put((uint8_t)a->dna_acgt);
+    w.put((uint8_t)a->has_table2);
+    for (int b = 0; b < 256; ++b) w.put(a->sym_of_byte[b]);
+    for (int b = 0; b < 256; ++b) w.put(a->byte_of_sym[b]);
+    w.put(a->build_ms);
+    for (const HostSubset &h : a->subs) {
+        w.put(h.id_lo);
+        w.put(h.id_hi);
+        w.put(h.max_len);
+        w.put(h.states);
+        w.put(h.rows16);
+        w.put(h.rows_e16);
+        for (double t : h.tail_mass) w.put(t);
+        w.vec(h.table);
+        w.vec(h.fail);
+        w.vec(h.depth);
+        w.vec(h.out_off);
+        w.vec(h.out_ids);
+        w.vec(h.table2);
+        w.vec(h.table16);
+        w.vec(h.table_e16);
+    }
+    const bool ok = w.ok && fflush(f) == 0;
+    if (fclose(f) != 0 || !ok) return set_error(AC_EINVAL, "ac_save: write to %s failed", path);
+    return AC_OK;
+}
+
+int ac_load(const char *path, int device, ac_automaton **out) {
+    NvtxRange nvtx_range("ac_load");
+    if (!path || !out) return set_error(AC_EINVAL, "ac_load: NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return set_error(AC_EINVAL, "ac_load: cannot open %s", path);
+    uint64_t size = 0;
+    if (fseek(f, 0, SEEK_END) == 0) {
+        const long e = ftell(f);
+        size = e > 0 ? (uint64_t)e : 0;
+    }
+    fseek(f, 0, SEEK_SET);
+    ac_automaton *a = new (std::nothrow) ac_automaton();
+    if (!a) {
+        fclose(f);
+        return set_error(AC_ENOMEM, "ac_load: host allocation");
+    }
+    int rc = AC_OK;
+    try {
+        FileReader r{f, size};
+        char magic[8] = {};
+        uint32_t format = 0;
+        for (char &c : magic) r.get(c);
+        r.get(format);
+        if (!r.ok || memcmp(magic, kFileMagic, 8) != 0 || format != kFileFormat) {
+            rc = set_error(AC_EINVAL, "ac_load: %s is not an automaton file of this library", path);
+        } else {
+            uint8_t acgt = 0, t2 = 0;
+            r.get(a->P);
+            r.get(a->K);
+            r.get(a->sigma);
+            r.get(a->max_len);
+            r.get(a->placement);
+            r.get(a->machine);
+            r.get(a->smem_cap_bytes);
+            r.get(acgt);
+            r.get(t2);
+            a->dna_acgt = acgt != 0;
+            a->has_table2 = t2 != 0;
+            for (int b = 0; b < 256; ++b) r.get(a->sym_of_byte[b]);
+            for (int b = 0; b < 256; ++b) r.get(a->byte_of_sym[b]);
+            r.get(a->build_ms);
+            if (r.ok && (a->K == 0 || a->K > a->P)) r.ok = false;
+            if (r.ok) a->subs.resize(a->K);
+            for (uint32_t k = 0; r.ok && k < a->K; ++k) {
+                HostSubset &h = a->subs[k];
+                r.get(h.id_lo);
+                r.get(h.id_hi);
+                r.get(h.max_len);
+                r.get(h.states);
+                r.get(h.rows16);
+                r.get(h.rows_e16);
+                for (double &t : h.tail_mass) r.get(t);
+                r.vec(h.table);
+                r.vec(h.fail);
+                r.vec(h.depth);
+                r.vec(h.out_off);
+                r.vec(h.out_ids);
+                r.vec(h.table2);
+                r.vec(h.table16);
+                r.vec(h.table_e16);
+            }
+            if (!r.ok || r.left != 0) {
+                rc = set_error(AC_EINVAL, "ac_load: %s is truncated or has trailing bytes", path);
+            } else if (const char *why = check_loaded(a)) {
+                rc = set_error(AC_EINVAL, "ac_load: %s: %s", path, why);
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        rc = set_error(AC_ENOMEM, "ac_load: host allocation");
+    }
+    fclose(f);
+    if (rc == AC_OK) {
+        a->device = device;
+        if (device >= 0) {
+            rc = upload(a);
+            if (rc == AC_OK) rc = check_smem_placement(a);
+        }
+    }
+    if (rc != AC_OK) {
+        free_device(a);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return AC_OK;
 }
 
 int ac_stats(const ac_automaton *a, ac_stats_t *o) {

@@ -406,3 +406,75 @@ def test_ac_log_levels():
     one = run(1)
     assert one and all("error" in l for l in one)
     assert run(None) == []
+
+
+def _views(a):
+    st = A.ac_stats(a)
+    out = []
+    for k in range(st["num_subsets"]):
+        v = A.ac_subset(a, k)
+        out.append({f: (None if v[f] is None else np.asarray(v[f]).copy()) if isinstance(v[f], np.ndarray) or v[f] is None
+                     else v[f] for f in v})
+    return st, out
+
+
+def _same_machines(a, b):
+    sa, va = _views(a)
+    sb, vb = _views(b)
+    for f in ("num_patterns", "num_subsets", "sigma", "max_len", "states", "table_bytes", "output_entries",
+              "table2_bytes"):
+        assert sa[f] == sb[f], f
+    for x, y in zip(va, vb):
+        assert x.keys() == y.keys()
+        for f in x:
+            if isinstance(x[f], np.ndarray):
+                assert isinstance(y[f], np.ndarray) and np.array_equal(x[f], y[f]), f
+            else:
+                assert x[f] == y[f], f
+
+
+def test_save_and_load_round_trip(tmp_path):
+    """ac_save / ac_load (host-only automata: no GPU needed): the loaded
+    machines equal the saved ones table for table, for one machine, subsets,
+    the two-symbol table, the failure-less machine and a 20-letter alphabet."""
+    rng = np.random.default_rng(12)
+    text, pats = workloads.tiny_case(rng, b"ACGT", max_n=3000, max_p=40, max_len=12)
+    prot = [bytes(rng.choice(np.frombuffer(workloads.PROTEIN, np.uint8), size=int(rng.integers(2, 9))))
+            for _ in range(50)]
+    cases = [dict(patterns=pats, alphabet="ACGT"), dict(patterns=pats, alphabet="ACGT", num_subsets=3),
+             dict(patterns=pats, alphabet="ACGT", stride=2), dict(patterns=pats, alphabet="ACGT",
+                                                                 machine=A.AC_MACHINE_PFAC),
+             dict(patterns=prot, alphabet=workloads.PROTEIN)]
+    for i, kw in enumerate(cases):
+        a = A.ac_build(device=-1, **kw)
+        path = tmp_path / f"m{i}.acm"
+        A.ac_save(a, path)
+        b = A.ac_load(path, device=-1)
+        _same_machines(a, b)
+
+
+def test_load_refuses_bad_files(tmp_path):
+    pats = [b"ACGT", b"CG", b"TTA"]
+    a = A.ac_build(pats, alphabet="ACGT", device=-1)
+    good = tmp_path / "good.acm"
+    A.ac_save(a, good)
+    data = good.read_bytes()
+
+    def refused(blob, name):
+        p = tmp_path / name
+        p.write_bytes(blob)
+        with pytest.raises(A.AcError) as e:
+            A.ac_load(p, device=-1)
+        assert e.value.code == A.AC_EINVAL
+
+    refused(data[:-5], "truncated.acm")
+    refused(data + b"\0", "trailing.acm")
+    refused(b"NOTAFILE" + data[8:], "magic.acm")
+    # the first table entry (after the header and the subset's scalars) points past the machine
+    first = 8 + 4 + 16 + 8 + 4 + 2 + 512 + 8 + 24 + 32 * 8 + 8
+    bad = bytearray(data)
+    bad[first:first + 4] = (0x7FFFFFF0).to_bytes(4, "little")
+    refused(bytes(bad), "transition.acm")
+    with pytest.raises(A.AcError) as e:
+        A.ac_load(tmp_path / "missing.acm", device=-1)
+    assert e.value.code == A.AC_EINVAL
