@@ -397,8 +397,9 @@ int ac_build(const uint8_t *const *pats, const uint32_t *lens, uint32_t P, const
     a->device = opts ? opts->device : 0;
     a->smem_cap_bytes = opts ? opts->smem_table_bytes : 0;
     if (a->placement < AC_PLACE_AUTO || a->placement > AC_PLACE_HYBRID16) {
+        const int placement = a->placement;
         delete a;
-        return set_error(AC_EINVAL, "ac_build: unknown placement %d", a->placement);
+        return set_error(AC_EINVAL, "ac_build: unknown placement %d", placement);
     }
     int rc;
     try {

@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t short_step(uint32_t s, uint32_t c, const uin
 // MAXW: words of the window a thread holds (warm-up + row words <= MAXW).
 template <int FMT, int SM, int MAXW>
 __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ ScanParams p) {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     const SubsetDev &sd = *p.subs;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warm_bytes = (FMT == FMT_U8) ? sd.warm : (sd.warm + 3) / 4;
