@@ -2,7 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define AC_HAVE_NVTX 1
+#endif
 #include <stdint.h>
 
 #include <atomic>
@@ -122,8 +125,12 @@ uint32_t scan_stride(const ac_automaton *a, int fmt, uint32_t want);
 
 // A named NVTX range over a host phase (a no-op unless a profiler records NVTX).
 struct NvtxRange {
+#ifdef AC_HAVE_NVTX
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
     ~NvtxRange() { nvtxRangePop(); }
+#else  // a toolkit without the NVTX headers: no ranges
+    explicit NvtxRange(const char *) {}
+#endif
     NvtxRange(const NvtxRange &) = delete;
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
