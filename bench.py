@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "AC scan text GB/s"
+L2_SECTOR_CEILING_G = 175.0  # measured ceiling of random 32-byte L2 sector reads on a GB300 (G/s)
 UNIT = "GB/s"
 
 
@@ -230,9 +231,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_key: str):
-    """DRAM bytes per launch of the scan kernel from a committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def ncu_per_launch(workload_key: str, field: str = "dram_bytes"):
+    """A per-launch counter of the scan kernel (DRAM bytes, L2 read sectors)
+    from a committed ncu summary, if it was taken on the current kernel
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "scan_kernel_traffic.json")
     if not os.path.exists(path):
         return None
@@ -241,7 +243,11 @@ def ncu_traffic(workload_key: str):
     if d.get("kernel_source_sha") != kernel_source_hash():
         return None
     e = d.get("per_launch", {}).get(workload_key)
-    return e.get("dram_bytes") if e else None
+    return e.get(field) if e else None
+
+
+def ncu_traffic(workload_key: str):
+    return ncu_per_launch(workload_key, "dram_bytes")
 
 
 def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
@@ -703,6 +709,16 @@ def main():
                 "roofline_ms": max(t_hbm, t_lookup) * 1e3,
                 "frac_of_roofline_time": max(t_hbm, t_lookup) / scan_s,
                 "lookup_peak_per_s": lookup_rate_peak, "lookups_per_launch": lookups}
+    # the bound that holds in practice: L2 read requests (table rows beyond
+    # shared memory, text stages), per launch from the ncu summary, over the
+    # live kernel time, against the measured ceiling of random 32-byte L2 reads
+    sectors = ncu_per_launch(key, "l2_read_sectors")
+    if sectors:
+        roofline["l2_requests"] = {"sectors_per_launch": sectors,
+                                   "achieved_gsectors_per_s": sectors / scan_s / 1e9,
+                                   "ceiling_gsectors_per_s": L2_SECTOR_CEILING_G,
+                                   "frac": sectors / scan_s / 1e9 / L2_SECTOR_CEILING_G,
+                                   "ceiling_source": "random 32-byte L2 reads (two-symbol table scan), GB300"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
