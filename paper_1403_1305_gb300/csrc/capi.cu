@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <chrono>
 #include <mutex>
 
@@ -92,7 +93,26 @@ static cudaMemPool_t pool_for(int device) {
     return g_pools[device];
 }
 
+// Fault injection for tests (environment, read once): AC_FAULT_ALLOC=N lets
+// N device scratch allocations succeed and fails every later one, so the
+// calls' out-of-memory paths (AC_ENOMEM, nothing launched on a missing
+// buffer) run without a real shortage.
+static bool scratch_allowed() {
+    static std::once_flag once;
+    static bool injected = false;
+    static std::atomic<int64_t> left{0};
+    std::call_once(once, [] {
+        const char *v = getenv("AC_FAULT_ALLOC");
+        if (v && *v) {
+            injected = true;
+            left = std::max<int64_t>(0, atoll(v));
+        }
+    });
+    return !injected || left.fetch_sub(1) > 0;
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t stream) {
+    if (!scratch_allowed()) return nullptr;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaMemPool_t p = pool_for(dev);
