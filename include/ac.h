@@ -336,11 +336,16 @@ AC_API int ac_sort_keys_async(const ac_automaton *a, uint64_t n, uint64_t *d_key
  * an allocation's implicit synchronisation or lock, or a host application
  * that forbids the library any allocation. This entry point allocates
  * nothing; its scratch is one fixed array of about 8.1 MiB compiled into the
- * library, which every GPU that loads the library keeps until the process
- * exits. Limits: cap <= 262,144 match records (larger cap: AC_ERANGE); the
- * text must be 16-byte aligned unless it is at most 65,536 bytes (else
- * AC_EINVAL). The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * library. A device holds that array from the first ac_scan_noalloc call on
+ * it until the process exits: the first call on a device loads this part of
+ * the library's device code and reserves the array (through
+ * cudaGetSymbolAddress), so make it at initialisation -- a call with n = 0
+ * and cap = 0 does it -- before the device's memory is committed elsewhere
+ * and before any stream capture. If that first lookup fails (AC_ENOMEM when
+ * the device has no room, else AC_ECUDA), nothing is kept and the next call
+ * tries again. Limits: cap <= 262,144 match records (larger cap:
+ * AC_ERANGE); the text must be 16-byte aligned unless it is at most 65,536
+ * bytes (else AC_EINVAL).
  * Every call uses the same array, which keeps the previous call's contents
  * (the call clears what must start at zero): calls that overlap on the GPU,
  * from any stream or thread, race and must be serialised by the caller.

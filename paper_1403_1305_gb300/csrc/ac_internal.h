@@ -135,6 +135,11 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Limit (ns) of the bounded device-side waits of the next scan launch: 2 s,
+// or 0 (the launch's first wait gives up) for the next N launches when the
+// environment sets AC_FAULT_WAIT=N (read once; capi.cu).
+uint64_t wait_limit_ns();
+
 // error reporting and the AC_LOG diagnostics (capi.cu)
 int set_error(int code, const char *fmt, ...);
 int log_level();

@@ -111,6 +111,23 @@ static bool scratch_allowed() {
     return !injected || left.fetch_sub(1) > 0;
 }
 
+// Limit of the bounded device-side waits (mbarrier waits on TMA copies) of a
+// scan launch: 2 s. Fault injection for tests (environment, read once):
+// AC_FAULT_WAIT=N gives the next N launches with such waits a limit of 0, so
+// each gives up at its first wait, sets the error word, lets the copies it
+// issued land and exits (the call reports AC_ETIMEDOUT); later launches get
+// the normal limit. No wait is left unbounded and nothing faults.
+uint64_t wait_limit_ns() {
+    static std::once_flag once;
+    static std::atomic<int64_t> left{0};
+    std::call_once(once, [] {
+        const char *v = getenv("AC_FAULT_WAIT");
+        if (v && *v) left = std::max<int64_t>(0, atoll(v));
+    });
+    if (left.load(std::memory_order_relaxed) > 0 && left.fetch_sub(1) > 0) return 0;
+    return 2000000000ull;
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t stream) {
     if (!scratch_allowed()) return nullptr;
     int dev = 0;

@@ -14,8 +14,13 @@
 // (about 8.1 MiB): the match counter and error word, the unsorted keys and
 // the sort's second buffer for up to kNoAllocMaxMatches matches, the radix
 // sort's temporary storage, and a small staging area for texts that are not
-// 16-byte aligned or shorter than 64 bytes. Every GPU that loads the library
-// holds this array until the process exits.
+// 16-byte aligned or shorter than 64 bytes. A device holds this array from
+// the first ac_scan_noalloc call on it (which loads this part of the
+// library's device code and reserves the array) until the process exits, so
+// make that first call at initialisation -- a call with n = 0 and cap = 0
+// does it -- before the device's memory is committed elsewhere and before any
+// stream capture.
+#include <atomic>
 #include <mutex>
 
 #include "ac_internal.h"
@@ -35,21 +40,32 @@ constexpr uint64_t kNoAllocScratchBytes = kTextOff + kNoAllocTextBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device with that
+// Device address of g_noalloc_scratch on each device, looked up with that
 // device current (in host code the array's name is only a host-side handle).
+// The library's code for a device is loaded lazily, so the first lookup on a
+// device loads this file's module and reserves the array's memory then; it
+// can fail (for instance with cudaErrorMemoryAllocation when another
+// allocator already holds the device's memory). Only a successful lookup is
+// kept: a failed one clears the runtime's error state, is reported, and the
+// next call tries again.
 constexpr int kMaxDevices = 64;
-static std::once_flag g_once[kMaxDevices];
-static unsigned char *g_addr[kMaxDevices];
-static cudaError_t g_setup_err[kMaxDevices];
+static std::mutex g_addr_mu;
+static std::atomic<unsigned char *> g_addr[kMaxDevices];
 
 unsigned char *scratch_on(int device, cudaError_t *err) {
-    std::call_once(g_once[device], [device] {
-        void *p = nullptr;
-        g_setup_err[device] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        g_addr[device] = g_setup_err[device] == cudaSuccess ? (unsigned char *)p : nullptr;
-    });
-    *err = g_setup_err[device];
-    return g_addr[device];
+    *err = cudaSuccess;
+    if (unsigned char *p = g_addr[device].load(std::memory_order_acquire)) return p;
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (unsigned char *p = g_addr[device].load(std::memory_order_acquire)) return p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();  // do not leave the error for another entry point's launch check
+        *err = e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        return nullptr;
+    }
+    g_addr[device].store((unsigned char *)p, std::memory_order_release);
+    return (unsigned char *)p;
 }
 
 uint32_t value_bits(uint64_t x) {
@@ -97,7 +113,9 @@ extern "C" int ac_scan_noalloc(const ac_automaton *a, const uint8_t *d_text, uin
     if (!dev.ok) return set_error(AC_ECUDA, "ac_scan_noalloc: cannot use device %d", a->device);
     cudaError_t e;
     unsigned char *base = scratch_on(a->device, &e);
-    if (!base) return set_error(AC_ECUDA, "ac_scan_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    if (!base)
+        return set_error(e == cudaErrorMemoryAllocation ? AC_ENOMEM : AC_ECUDA,
+                         "ac_scan_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
 
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *num = (unsigned long long *)base;

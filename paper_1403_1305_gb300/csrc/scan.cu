@@ -552,6 +552,7 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
     p.num = o.num;
     p.counts = o.counts;
     p.err = o.err;
+    p.wait_ns = wait_limit_ns();
     p.key_shift = b.key_shift;
     p.tail_bytes = 0;
     p.items = b.items;
@@ -619,6 +620,7 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
     p.num = o.num;
     p.counts = o.counts;
     p.err = o.err;
+    p.wait_ns = wait_limit_ns();
     p.key_shift = (uint32_t)key_shift_for(a);
     p.smem_rows = plan.smem_rows;
     p.table_words = plan.table_words;
@@ -753,6 +755,7 @@ int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, cons
     p.num = o.num;
     p.counts = o.counts;
     p.err = o.err;
+    p.wait_ns = wait_limit_ns();
     p.key_shift = (uint32_t)key_shift_for(a);
     memcpy(p.sym_of_byte, a->sym_of_byte, 256);
     const uint64_t row_blocks = (p.row_end - p.row_begin + p.rows_per_tile - 1) / p.rows_per_tile;

@@ -86,6 +86,7 @@ struct ScanParams {
     unsigned long long *num;
     unsigned long long *counts;
     uint32_t *err;
+    uint64_t wait_ns;       // limit of every bounded device-side wait; 0 gives up at the first wait
     // batch mode (several texts in one arena of whole rows)
     const BatchItemDev *items;  // sorted by first row
     const BatchTileDev *tiles;  // one per tile: machine and first row
@@ -167,13 +168,18 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Bounded wait on an mbarrier phase: false (and the error word set) after 2 s.
-__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, uint32_t *err) {
+// Bounded wait on an mbarrier phase: false (and the error word set) once
+// `limit` ns have passed; a limit of 0 gives up before the first check.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, uint32_t *err, uint64_t limit) {
+    if (limit == 0) {
+        atomicOr(err, 1u);
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+        if ((it & 255u) == 0 && global_ns() - t0 > limit) {
             atomicOr(err, 1u);
             return false;
         }
@@ -558,7 +564,7 @@ __global__ void __launch_bounds__(512, 1)
 
         for (uint32_t s = 0; s < nst; ++s) {
             const uint32_t slot = s % kNS;
-            if (!wait_phase(my_bars + slot, (parity >> slot) & 1u, p.err)) {
+            if (!wait_phase(my_bars + slot, (parity >> slot) & 1u, p.err, p.wait_ns)) {
                 aborted = true;
                 break;
             }

@@ -84,13 +84,18 @@ __device__ __forceinline__ bool mbar_try_wait_s(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: false (and the error word set) after 2 s.
-__device__ __forceinline__ bool wait_phase_s(uint32_t bar, uint32_t parity, uint32_t *err) {
+// Bounded wait on an mbarrier phase: false (and the error word set) once
+// `limit` ns have passed; a limit of 0 gives up before the first check.
+__device__ __forceinline__ bool wait_phase_s(uint32_t bar, uint32_t parity, uint32_t *err, uint64_t limit) {
+    if (limit == 0) {
+        atomicOr(err, 1u);
+        return false;
+    }
     if (mbar_try_wait_s(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait_s(bar, parity)) return true;
-        if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+        if ((it & 255u) == 0 && global_ns() - t0 > limit) {
             atomicOr(err, 1u);
             return false;
         }
@@ -231,6 +236,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (threadIdx.x == 0) {
         for (uint32_t i = 0; i <= nwarps; ++i) mbar_init(bars + i, 1);  // one per warp, one for the table
         // table copy state: [0] = the last copy landed, [1] = barrier phase | (a copy is late) << 1
+        reinterpret_cast<uint32_t *>(tbars + 1)[0] = 1;
         reinterpret_cast<uint32_t *>(tbars + 1)[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(NT, 1)
                         reinterpret_cast<const uint8_t *>(sdp->table_e16) + bulk));
                 if (bulk) {
                     const uint32_t st = tw[1];
-                    ok = wait_phase_s(tbar, st & 1u, p.err) ? 1u : 0u;
+                    ok = wait_phase_s(tbar, st & 1u, p.err, p.wait_ns) ? 1u : 0u;
                     tw[1] = ok ? (st ^ 1u) : (st | 2u);
                 }
                 tw[0] = ok;
@@ -369,7 +375,7 @@ __global__ void __launch_bounds__(NT, 1)
 
         for (uint32_t s = 0; s < nst; ++s) {
             if (copies) {
-                if (!wait_phase_s(my_bar, parity & 1u, p.err)) {
+                if (!wait_phase_s(my_bar, parity & 1u, p.err, p.wait_ns)) {
                     aborted = true;
                     return;
                 }
@@ -517,7 +523,10 @@ __global__ void __launch_bounds__(NT, 1)
             if (row0 < p.row_end) run_rows(sdp, hot, row0);
         }
     }
-    if (aborted && lane == 0) {
+    // A warp that gave up inside run_rows has a text copy in flight; one that
+    // stopped because a table copy was late (state word [0] = 0) has none
+    // (every earlier row block waited for all of its copies).
+    if (aborted && lane == 0 && reinterpret_cast<volatile uint32_t *>(tbars + 1)[0] != 0) {
         // let a copy already issued by this warp land before the CTA exits (bounded)
         const uint64_t t0 = global_ns();
         while (!mbar_try_wait_s(my_bar, parity & 1u) && global_ns() - t0 < 100000000ull) {

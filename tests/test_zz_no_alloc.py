@@ -77,3 +77,84 @@ def test_capacity_beyond_the_fixed_limit_is_refused():
     with pytest.raises(A.AcError) as e:
         run(A.ac_scan_noalloc, a, d, 64, (1 << 18) + 1)
     assert e.value.code == A.AC_ERANGE
+
+
+def test_empty_text_and_zero_capacity():
+    """n = 0 (the set-up call a caller makes at initialisation) and cap = 0
+    (count only): the counter and the counts come back right although the
+    shared array still holds the previous call's contents."""
+    w = workloads.config1()
+    a = A.ac_build(w.patterns, alphabet="ACGT")
+    d = torch.from_numpy(w.text).cuda()
+    M, _, c = run(A.ac_scan_noalloc, a, d, w.text.size, 8192)      # leaves matches in the array
+    assert M > 0
+    d_num = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+    d_c = torch.full((a.num_patterns,), 7, dtype=torch.int64, device="cuda")
+    A.ac_scan_noalloc(a, d, 0, A.AC_U8, None, None, 0, d_num, d_c)
+    torch.cuda.synchronize()
+    assert int(d_num.item()) == 0 and int(d_c.abs().sum().item()) == 0
+    A.ac_scan_noalloc(a, d, w.text.size, A.AC_U8, None, None, 0, d_num, d_c)
+    torch.cuda.synchronize()
+    assert int(d_num.item()) == M and np.array_equal(d_c.cpu().numpy(), c)
+
+
+CHILD = r'''
+import hashlib, json, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+import workloads
+from paper_1403_1305_gb300 import ac as A
+torch.cuda.set_device(0)
+w = workloads.config1()
+a = A.ac_build(w.patterns, alphabet="ACGT")   # tables from cudaMalloc, not the scratch allocator
+d = torch.from_numpy(w.text).cuda()
+d_m = torch.zeros(2 * 8192, dtype=torch.int32, device="cuda")
+d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+d_c = torch.zeros(a.num_patterns, dtype=torch.int64, device="cuda")
+out = {{}}
+try:
+    A.ac_scan_async(a, d, w.text.size, A.AC_U8, None, d_m, 8192, d_num, d_c)
+    out["async"] = 0
+except A.AcError as e:
+    out["async"] = e.code
+for k in range(2):
+    A.ac_scan_noalloc(a, d, w.text.size, A.AC_U8, None, d_m, 8192, d_num, d_c)
+    torch.cuda.synchronize()
+    M = int(d_num.item())
+    h = hashlib.sha256(d_m.view(-1, 2)[:M].cpu().numpy().tobytes() + d_c.cpu().numpy().tobytes()).hexdigest()
+    out["noalloc%d" % k] = [M, h]
+print(json.dumps(out))
+'''
+
+
+def test_allocates_nothing():
+    """With every scratch allocation of the library made to fail
+    (AC_FAULT_ALLOC=0), ac_scan_async reports AC_ENOMEM while
+    ac_scan_noalloc still scans, twice, to the same result as an
+    unrestricted run."""
+    import hashlib
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env["AC_FAULT_ALLOC"] = "0"
+    env.pop("AC_FAULT_WAIT", None)
+    r = subprocess.run([sys.executable, "-c", CHILD.format(root=root)], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["async"] == A.AC_ENOMEM, out
+    w = workloads.config1()
+    a = A.ac_build(w.patterns, alphabet="ACGT")
+    d = torch.from_numpy(w.text).cuda()
+    d_m = torch.zeros(2 * 8192, dtype=torch.int32, device="cuda")
+    d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_c = torch.zeros(a.num_patterns, dtype=torch.int64, device="cuda")
+    A.ac_scan_async(a, d, w.text.size, A.AC_U8, None, d_m, 8192, d_num, d_c)
+    torch.cuda.synchronize()
+    M = int(d_num.item())
+    h = hashlib.sha256(d_m.view(-1, 2)[:M].cpu().numpy().tobytes() + d_c.cpu().numpy().tobytes()).hexdigest()
+    assert out["noalloc0"] == [M, h] and out["noalloc1"] == [M, h], (out, M)
