@@ -528,8 +528,19 @@ const char *check_loaded(const ac_automaton *a) {
     if (a->sigma == 0 || a->sigma > 255 || a->K == 0 || a->K > a->P || a->subs.size() != a->K)
         return "bad alphabet size or subset count";
     if (a->machine != AC_MACHINE_DFA && a->machine != AC_MACHINE_PFAC) return "unknown machine";
-    for (int b = 0; b < 256; ++b)
+    uint32_t mapped = 0;
+    for (int b = 0; b < 256; ++b) {
         if (a->sym_of_byte[b] > a->sigma) return "bad symbol map";
+        if (a->sym_of_byte[b] < a->sigma) ++mapped;
+    }
+    // every symbol has exactly one byte, and byte_of_sym is the inverse map
+    if (mapped != a->sigma) return "the symbol map does not give every symbol exactly one byte";
+    for (uint32_t c = 0; c < a->sigma; ++c)
+        if (a->sym_of_byte[a->byte_of_sym[c]] != c) return "byte_of_sym does not invert the symbol map";
+    // the kernels decode A, C, G, T bytes by a fixed code when this flag is set
+    const bool acgt = a->sigma == 4 && a->byte_of_sym[0] == 'A' && a->byte_of_sym[1] == 'C' &&
+                      a->byte_of_sym[2] == 'G' && a->byte_of_sym[3] == 'T';
+    if (acgt != a->dna_acgt) return "the ACGT flag disagrees with the alphabet";
     uint32_t next_id = 0, max_len = 0;
     for (const HostSubset &h : a->subs) {
         const uint64_t S = h.states;

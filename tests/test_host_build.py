@@ -475,6 +475,19 @@ def test_load_refuses_bad_files(tmp_path):
     bad = bytearray(data)
     bad[first:first + 4] = (0x7FFFFFF0).to_bytes(4, "little")
     refused(bytes(bad), "transition.acm")
+    # header: magic 8, format 4, P K sigma max_len placement machine smem_cap (4 each), ACGT flag, table2
+    # flag, then sym_of_byte[256] and byte_of_sym[256]
+    flag, sym, inv = 8 + 4 + 7 * 4, 8 + 4 + 7 * 4 + 2, 8 + 4 + 7 * 4 + 2 + 256
+    assert data[flag] == 1 and data[inv:inv + 4] == b"ACGT" and data[sym + ord("A")] == 0
+    bad = bytearray(data)
+    bad[flag] = 0                                   # ACGT flag that disagrees with the alphabet
+    refused(bytes(bad), "acgt_flag.acm")
+    bad = bytearray(data)
+    bad[sym + ord("A")], bad[sym + ord("C")] = 1, 0  # map no longer inverted by byte_of_sym
+    refused(bytes(bad), "inverse.acm")
+    bad = bytearray(data)
+    bad[sym + ord("N")] = 2                          # a second byte for symbol 2
+    refused(bytes(bad), "two_bytes.acm")
     with pytest.raises(A.AcError) as e:
         A.ac_load(tmp_path / "missing.acm", device=-1)
     assert e.value.code == A.AC_EINVAL
