@@ -42,7 +42,6 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "AC scan text GB/s"
-L2_SECTOR_CEILING_G = 175.0  # measured ceiling of random 32-byte L2 sector reads on a GB300 (G/s)
 UNIT = "GB/s"
 
 
@@ -322,6 +321,31 @@ def time_async(A, torch, a, d_text, n, fmt, reps, warm=3):
     return float(np.median(ts)), M, cap, d_m, d_num, d_counts
 
 
+def bench_lookup_ceilings(A, dev, table_sizes):
+    """Dependent random 4-byte lookups per second (ac_probe_gather): a table
+    in shared memory (160 KB, the bank-conflict ceiling of one lookup per
+    lane), in global memory at the scan tables' sizes (L2-resident when they
+    fit) and at 1 GiB (HBM), with 1,024 to 8,192 chains per SM; plus the
+    latency of one dependent lookup (one warp, one chain per lane). Each
+    random lookup outside shared memory is one 32-byte sector request."""
+    out = {"method": "ac_probe_gather: one CTA of 1,024 threads per SM, chains x[j] <- T[hi32(x[j] * words)] + step, "
+                     "table of seeded pseudo-random words; CUDA events around one launch after a warm-up launch"}
+    sm = A.ac_probe_gather(dev, 160 << 10, shared=True, threads=1024, chains=4, steps=4096)
+    out["smem_160KB"] = {"lookups_per_s": sm["gathers_per_s"], "chains_per_sm": sm["chains_per_sm"],
+                         "ms": sm["ms"]}
+    for name, nbytes in table_sizes:
+        rows = []
+        for chains in (1, 2, 4, 8):
+            r = A.ac_probe_gather(dev, nbytes, shared=False, threads=1024, chains=chains, steps=1024)
+            rows.append({"chains_per_sm": r["chains_per_sm"], "lookups_per_s": r["gathers_per_s"]})
+        lat = A.ac_probe_gather(dev, nbytes, shared=False, threads=32, chains=1, steps=4096)
+        best = max(rows, key=lambda r: r["lookups_per_s"])
+        out[name] = {"table_bytes": int(nbytes), "sweep": rows, "best_lookups_per_s": best["lookups_per_s"],
+                     "best_chains_per_sm": best["chains_per_sm"],
+                     "latency_ns": lat["ms"] * 1e6 / 4096}
+    return out
+
+
 def bench_configs(A, torch, dev, hbm_peak):
     """Config 1 (1 MiB DNA, 100 patterns) and config 3 (64 MiB protein,
     100,000 patterns, table in L2)."""
@@ -378,9 +402,17 @@ def bench_configs(A, torch, dev, hbm_peak):
     st = A.ac_stats(a)
     d = torch.from_numpy(w.text).to(f"cuda:{dev}")
     ms, M, *_ = time_async(A, torch, a, d, w.text.size, A.AC_U8, 10)
+    # its table (77 MB) is read through L2: the ceiling is random 4-byte reads from a buffer of that size
+    probe = max((A.ac_probe_gather(dev, st["table_bytes"], shared=False, threads=1024, chains=c, steps=1024)
+                 for c in (2, 4, 8)), key=lambda r: r["gathers_per_s"])
+    lk = w.text.size / (ms * 1e-3)
     out["config3"] = {"workload": w.name, "matches": M, "states": st["states"], "table_bytes": st["table_bytes"],
                       "smem_states": st["smem_states"], "median_ms": ms, "GBps": w.text.size / ms / 1e6,
-                      "frac_of_hbm": w.text.size / ms / 1e6 / hbm_peak, "build_ms": st["build_ms"]}
+                      "frac_of_hbm": w.text.size / ms / 1e6 / hbm_peak, "build_ms": st["build_ms"],
+                      "lookups_per_s": lk, "l2_lookup_ceiling_per_s": probe["gathers_per_s"],
+                      "frac_of_l2_lookup_ceiling": lk / probe["gathers_per_s"],
+                      "note": "whole scan (ac_scan_async: scan, sort, records) against one dependent lookup per "
+                              "symbol at the measured random-read rate of a buffer of the table's size"}
     return out
 
 
@@ -709,16 +741,26 @@ def main():
                 "roofline_ms": max(t_hbm, t_lookup) * 1e3,
                 "frac_of_roofline_time": max(t_hbm, t_lookup) / scan_s,
                 "lookup_peak_per_s": lookup_rate_peak, "lookups_per_launch": lookups}
+    # the ceilings the lookups meet, measured on this device: random 4-byte
+    # lookups in shared memory (bank conflicts), in L2 at this table's size,
+    # and in HBM
+    ceilings = bench_lookup_ceilings(A, dev, [("table", st["table_bytes"]), ("hbm_1GiB", 1 << 30)])
+    l2_ceiling = ceilings["table"]["best_lookups_per_s"]
+    smem_ceiling = ceilings["smem_160KB"]["lookups_per_s"]
+    roofline["lookups_per_s"] = lookups / scan_s
+    roofline["frac_of_measured_smem_lookup_ceiling"] = lookups / scan_s / smem_ceiling
     # the bound that holds in practice: L2 read requests (table rows beyond
     # shared memory, text stages), per launch from the ncu summary, over the
-    # live kernel time, against the measured ceiling of random 32-byte L2 reads
+    # live kernel time, against the measured ceiling of random 32-byte L2
+    # reads at this table's size
     sectors = ncu_per_launch(key, "l2_read_sectors")
     if sectors:
         roofline["l2_requests"] = {"sectors_per_launch": sectors,
                                    "achieved_gsectors_per_s": sectors / scan_s / 1e9,
-                                   "ceiling_gsectors_per_s": L2_SECTOR_CEILING_G,
-                                   "frac": sectors / scan_s / 1e9 / L2_SECTOR_CEILING_G,
-                                   "ceiling_source": "random 32-byte L2 reads (two-symbol table scan), GB300"}
+                                   "ceiling_gsectors_per_s": l2_ceiling / 1e9,
+                                   "frac": sectors / scan_s / l2_ceiling,
+                                   "ceiling_source": "ac_probe_gather: random 4-byte reads (one 32-byte sector "
+                                                     "each) over a buffer of the table's size, this device"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -734,7 +776,7 @@ def main():
                                           5: "16-bit prefix"}.get(st["scan_placement"], str(st["scan_placement"])),
                        "symbols_per_lookup": st["scan_stride"],
                        "scan_kernel": {1: "general", 2: "lean", 3: "short"}.get(st["scan_kernel"], str(st["scan_kernel"]))},
-            "roofline": roofline, "clocks": clocks,
+            "roofline": roofline, "lookup_ceilings": ceilings, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_note": "own kernels per step: scan, error mark, rank sort + record conversion "
                                  "(plus three memset nodes)"}
@@ -765,9 +807,13 @@ def main():
             av = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=K, device=dev)
             dt = torch.from_numpy(ht).to(f"cuda:{dev}")
             tt, ss, mm = time_device_path(A, torch, av, dt, n, fm, max(3, args.steps // 4), 2, pg, stream)
+            lk = K * n / max(1, A.ac_stats(av)["scan_stride"])  # dependent lookups per launch
             steps_v = max(3, args.steps // 4)
             var[f"K{K}-{f}"] = {"GBps": ht.size * steps_v / tt / 1e9, "symbols_per_s": n * steps_v / tt,
-                                "scan_ms": ss * 1e3, "matches": mm,
+                                "scan_ms": ss * 1e3, "matches": mm, "lookups_per_s": lk / ss,
+                                "symbols_per_lookup": A.ac_stats(av)["scan_stride"],
+                                "frac_of_nominal_smem_lookup_peak": lk / ss / lookup_rate_peak,
+                                "frac_of_measured_smem_lookup_ceiling": lk / ss / smem_ceiling,
                                 "smem_states": A.ac_stats(av)["smem_states"], "states": A.ac_stats(av)["states"]}
             del av, dt
         line["variants"] = var

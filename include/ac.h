@@ -463,6 +463,32 @@ AC_API int ac_serve_stats(ac_server *s, ac_serve_stats_t *out);
 /* Stop the scheduler (pending requests complete first) and release everything. */
 AC_API void ac_serve_destroy(ac_server *s);
 
+/* ------------------------------------------------------------ roofline probe */
+
+/* The lookup ceilings the scan meets (Section II.A: one dependent goto-table
+ * lookup per text symbol; the paper measures CPU throughput only, so this
+ * probe has no counterpart there). */
+typedef struct {
+    double ms;             /* device time of the timed launch (CUDA events) */
+    double gathers;        /* dependent 4-byte reads in it: sms * chains_per_sm * steps */
+    double gathers_per_s;
+    uint32_t chains_per_sm;
+    uint32_t sms;
+} ac_gather_probe;
+
+/* Measure dependent random 4-byte reads on device `device`: a table of
+ * table_bytes (seeded pseudo-random words, allocated and freed by the call)
+ * in global memory (shared = 0: served by L2 when the table fits there, else
+ * by HBM) or copied into each CTA's shared memory (shared = 1; the table must
+ * fit one CTA's shared memory, else AC_ERANGE). One CTA of `threads` threads
+ * per SM, each thread walking `chains` (1, 2, 4 or 8) independent chains of
+ * `steps` lookups, each lookup's address taken from the word the previous
+ * one read. One untimed warm-up launch precedes the timed one. Synchronous.
+ * Errors: AC_EINVAL (NULL out, threads not a multiple of 32 in [32, 1024],
+ * chains), AC_ERANGE, AC_ENOMEM, AC_ECUDA. */
+AC_API int ac_probe_gather(int device, uint64_t table_bytes, int shared, uint32_t threads, uint32_t chains,
+                           uint32_t steps, ac_gather_probe *out);
+
 /* ------------------------------------------------------------ misc */
 AC_API const char *ac_strerror(int code);
 AC_API const char *ac_last_error(void);

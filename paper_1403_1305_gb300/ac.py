@@ -35,7 +35,7 @@ EXPORTED = (
     "ac_build", "ac_free", "ac_save", "ac_load", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
     "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
-    "ac_version",
+    "ac_version", "ac_probe_gather",
 )
 
 
@@ -96,6 +96,11 @@ class ac_serve_opts(C.Structure):
                 ("staging", C.c_uint32)]
 
 
+class ac_gather_probe(C.Structure):
+    _fields_ = [("ms", C.c_double), ("gathers", C.c_double), ("gathers_per_s", C.c_double),
+                ("chains_per_sm", C.c_uint32), ("sms", C.c_uint32)]
+
+
 class ac_serve_stats_t(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("launches", C.c_uint64),
                 ("items_launched", C.c_uint64), ("queued", C.c_uint64), ("in_flight", C.c_uint64),
@@ -139,6 +144,7 @@ def _declare(lib):
         "ac_strerror": (C.c_char_p, [C.c_int]),
         "ac_last_error": (C.c_char_p, []),
         "ac_version": (C.c_int, []),
+        "ac_probe_gather": (C.c_int, [C.c_int, u64, C.c_int, u32, u32, u32, C.POINTER(ac_gather_probe)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -513,3 +519,13 @@ def ac_last_error() -> str:
 
 def ac_version() -> int:
     return lib().ac_version()
+
+
+def ac_probe_gather(device: int, table_bytes: int, shared: bool = False, threads: int = 1024, chains: int = 4,
+                    steps: int = 1024) -> dict:
+    """Dependent random 4-byte lookups per second from a table of
+    ``table_bytes`` in global memory (L2 or HBM) or shared memory."""
+    out = ac_gather_probe()
+    _check(lib().ac_probe_gather(int(device), int(table_bytes), int(bool(shared)), int(threads), int(chains),
+                                 int(steps), C.byref(out)), "ac_probe_gather")
+    return {f: getattr(out, f) for f, _ in ac_gather_probe._fields_}
