@@ -249,8 +249,13 @@ def ncu_traffic(workload_key: str):
     return ncu_per_launch(workload_key, "dram_bytes")
 
 
-def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
-    """Device-resident text: returns (total_s, scan_s_per_step, M)."""
+def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream, prewarm_s=0.3):
+    """Device-resident text: returns (total_s, scan_s_per_step, M).
+
+    Before the `warmup` steps, untimed steps run for `prewarm_s` seconds: on
+    a GB300 the first ~50 launches of a process run about 13% slower than
+    the steady state (clocks already at their maximum), so a handful of
+    warm-up steps alone would time that transient."""
     P = a.num_patterns
     d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
     d_counts = torch.zeros(P, dtype=torch.int64, device="cuda")
@@ -273,6 +278,12 @@ def time_device_path(A, torch, a, d_text, n, fmt, steps, warmup, pg, stream):
             ev1.record(stream)
         A.ac_sort_keys_async(a, n, d_keys, d_num, cap, stream, d_m, d_num)
 
+    t_end = time.perf_counter() + prewarm_s
+    while time.perf_counter() < t_end:
+        with torch.cuda.stream(stream):
+            for _ in range(10):
+                step()
+        stream.synchronize()
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             step()
@@ -309,6 +320,11 @@ def time_async(A, torch, a, d_text, n, fmt, reps, warm=3):
     cap = 1 << max(10, int(np.ceil(np.log2(max(M, 1) * 1.25 + 1))))
     d_m = torch.empty(cap, dtype=torch.int64, device="cuda")
     ts = []
+    with torch.cuda.stream(stream):  # untimed steady-state warm-up (see time_device_path)
+        t_end = time.perf_counter() + 0.1
+        while time.perf_counter() < t_end:
+            A.ac_scan_async(a, d_text, n, fmt, stream, d_m, cap, d_num, d_counts)
+            stream.synchronize()
     with torch.cuda.stream(stream):
         for i in range(warm + reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -572,15 +588,22 @@ def bench_serve(A, torch, dev, args):
     """16 resident automata (8 DNA x 5,000, 8 protein x 20,000 patterns);
     Poisson arrivals of texts with log-uniform lengths in [4 KiB, 64 MiB];
     rate raised x1.5 until throughput stops growing. Continuous batching
-    server against one synchronous ac_scan per request in arrival order, on
-    the same requests at the rate of the best throughput (median of three
-    runs each)."""
+    server against one synchronous ac_scan per request in arrival order.
+    Latency counts from each request's scheduled arrival in both arms (the
+    server is told it through ac_serve_submit_at), so queueing before the
+    server, or behind earlier requests in the per-request arm, is counted.
+    Request texts sit in page-locked host memory in both arms. Reported at
+    the rate of the best served throughput (median of three runs each) and
+    at the highest rate the server keeps up with (arrivals completed at
+    >= 85% of the offered rate)."""
     w = workloads.config5_sets()
     autos = [A.ac_build(s, alphabet=a, device=dev) for s, a in zip(w.pattern_sets, w.set_alphabet)]
     rng = np.random.default_rng(1055)
-    # one 64 MiB text per alphabet kind; a protein set's text maps Zipf ranks
-    # through that set's letter order (same law as drawing it directly)
-    dna_pool = workloads.dna_text(rng, 64 << 20)
+    # one 64 MiB text per alphabet kind, page-locked; a protein set's text maps
+    # Zipf ranks through that set's letter order (same law as drawing it directly)
+    def pinned(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    dna_pool = pinned(workloads.dna_text(rng, 64 << 20))
     ranks = None
     pools = []
     for letters, probs in w.set_letters:
@@ -589,7 +612,7 @@ def bench_serve(A, torch, dev, args):
             continue
         if ranks is None:
             ranks = workloads.iid_text(rng, 64 << 20, np.arange(len(letters), dtype=np.uint8), probs)
-        pools.append(np.asarray(letters, dtype=np.uint8)[ranks])
+        pools.append(pinned(np.asarray(letters, dtype=np.uint8)[ranks]))
 
     def make(count, rate):
         t, sets, lens = workloads.request_stream(rng, rate, count)
@@ -605,9 +628,11 @@ def bench_serve(A, torch, dev, args):
                                 device_mem_budget=8 << 30, staging=staging)
         tickets = [None] * len(reqs)
         start = time.perf_counter()
+        start_ns = time.monotonic_ns()
 
-        # several producer threads share the arrival stream (submit copies the
-        # text; one thread alone cannot copy fast enough at high rates)
+        # several producer threads share the arrival stream; each request is
+        # submitted at (or, when a producer lags, after) its scheduled time and
+        # carries that time as its arrival
         nprod = 4
         ths = []
         for k in range(nprod):
@@ -617,7 +642,7 @@ def bench_serve(A, torch, dev, args):
                     d = start + ta - time.perf_counter()
                     if d > 0:
                         time.sleep(d)
-                    tickets[i] = A.ac_serve_submit(srv, si, txt)
+                    tickets[i] = A.ac_serve_submit_at(srv, si, txt, start_ns + int(ta * 1e9))
             ths.append(threading.Thread(target=prod))
         for th in ths:
             th.start()
@@ -672,19 +697,89 @@ def bench_serve(A, torch, dev, args):
     served = nbytes / el_d / 1e9
     per_req = nbytes / el / 1e9
     kept = [r for r in sweep if r["kept_up"]]
-    return {"workload": w.name, "requests_per_rate": args.serve_requests, "sweep": sweep,
+    at_kept = None
+    if kept:
+        # both arms at the highest rate the server keeps up with
+        reqs_k = make(args.serve_requests, kept[-1]["rate_hz"])
+        nb_k = sum(r[2].size for r in reqs_k)
+        el_k, st_k = run_server(reqs_k)
+        el_kr, lat_k = run_per_request(reqs_k)
+        at_kept = {"rate_hz": kept[-1]["rate_hz"], "offered_req_per_s": len(reqs_k) / max(reqs_k[-1][0], 1e-9),
+                   "served_GBps": nb_k / el_k / 1e9, "served_req_per_s": len(reqs_k) / el_k,
+                   "served_p50_ms": st_k["p50_ms"], "served_p99_ms": st_k["p99_ms"],
+                   "per_request_GBps": nb_k / el_kr / 1e9, "per_request_req_per_s": len(reqs_k) / el_kr,
+                   "per_request_p50_ms": float(np.percentile(lat_k, 50)),
+                   "per_request_p99_ms": float(np.percentile(lat_k, 99)),
+                   "speedup": el_kr / el_k}
+    return {"workload": w.name, "requests_per_rate": args.serve_requests,
             "rate_hz_at_best": top["rate_hz"], "bytes_at_best": nbytes,
-            "highest_rate_kept_up": kept[-1]["rate_hz"] if kept else None,
-            "GBps_highest_rate_kept_up": kept[-1]["GBps"] if kept else None,
             "served_GBps": served, "served_p50_ms": st_d["p50_ms"], "served_p99_ms": st_d["p99_ms"],
             "served_mean_batch_items": st_d["mean_batch_items"],
             "served_pinned_staging_GBps": nbytes / el_p / 1e9, "served_pinned_staging_p50_ms": st_p["p50_ms"],
             "per_request_GBps": per_req, "per_request_p50_ms": float(np.percentile(lat, 50)),
             "per_request_p99_ms": float(np.percentile(lat, 99)),
-            "speedup": served / per_req,
-            "served_path": "ac_serve_* (3 streams, <=64 requests per launch, host texts copied into device memory "
-                           "by submit; 4 producer threads)",
-            "per_request_path": "ac_scan(host text) per request in arrival order"}
+            "speedup": served / per_req, "at_highest_rate_kept_up": at_kept,
+            "latency": "from each request's scheduled arrival to its result on the host, both arms",
+            "served_path": "ac_serve_* (3 streams, <=64 requests per launch, page-locked host texts copied into "
+                           "device memory by ac_serve_submit_at; 4 producer threads)",
+            "per_request_path": "ac_scan(page-locked host text) per request in arrival order",
+            "sweep": sweep}
+
+
+def _r(x, nd=3):
+    """x rounded to nd significant digits (None stays None)."""
+    if x is None or not isinstance(x, (int, float)):
+        return x
+    return float(f"{x:.{nd}g}")
+
+
+def summary(line):
+    """The figures of every section in a few hundred bytes, printed as the
+    line's last key so that a reader keeping only the end of the output
+    still has them."""
+    g = line.get
+    out = {"value_GBps": _r(g("value")), "scan_kernel_ms": _r(g("roofline", {}).get("kernel_ms")),
+           "frac_of_hbm": _r(g("roofline", {}).get("frac")), "e2e_GBps": _r((g("e2e") or {}).get("value"))}
+    lc = g("lookup_ceilings") or {}
+    if lc:
+        out["ceilings_G_lookups_per_s"] = {"smem": _r(lc["smem_160KB"]["lookups_per_s"] / 1e9),
+                                           "l2_table": _r(lc["table"]["best_lookups_per_s"] / 1e9),
+                                           "hbm": _r(lc["hbm_1GiB"]["best_lookups_per_s"] / 1e9)}
+    if g("variants"):
+        out["variants_scan_ms"] = {k: _r(v["scan_ms"]) for k, v in g("variants").items()}
+    c = g("configs") or {}
+    if "config1" in c:
+        c1 = c["config1"]
+        out["config1_us"] = {"one_call": _r(c1["single_call_device_ms"] * 1e3),
+                             "graph": _r((c1["graph_replayed_ms_per_scan"] or 0) * 1e3),
+                             "batch1000": _r(c1["batch1000_ms_per_scan"] * 1e3)}
+    if "config3" in c:
+        out["config3"] = {"ms": _r(c["config3"]["median_ms"]), "frac_l2": _r(c["config3"]["frac_of_l2_lookup_ceiling"])}
+    if g("pfac"):
+        out["pfac_scan_ms_dfa_vs_failureless"] = {k: [_r(v["dfa"]["scan_ms"]), _r(v["pfac"]["scan_ms"])]
+                                                  for k, v in g("pfac").items()}
+    if g("paper_shapes"):
+        out["paper_eq1_kBps"] = {k: {kk: _r(vv["eq1_Bps"] / 1e3) for kk, vv in v.items() if isinstance(vv, dict)}
+                                 for k, v in g("paper_shapes").items() if k.endswith("70KB")}
+    if g("embedded_check"):
+        out["embedded_time_ratio"] = _r(g("embedded_check")["time_ratio"])
+    b = g("batch")
+    if b:
+        out["batch"] = {"batched_GBps": _r(b["batched_GBps"]), "per_call_GBps": _r(b["per_call_GBps"]),
+                        "speedup": _r(b["speedup"])}
+    sv = g("serve")
+    if sv:
+        out["serve"] = {k: _r(sv.get(k)) for k in ("served_GBps", "per_request_GBps", "speedup", "served_p50_ms",
+                                                   "served_p99_ms", "per_request_p50_ms", "per_request_p99_ms")}
+        k = sv.get("at_highest_rate_kept_up")
+        if k:
+            out["serve_kept_up"] = {kk: _r(k[kk]) for kk in ("rate_hz", "served_GBps", "per_request_GBps", "speedup",
+                                                             "served_p50_ms", "served_p99_ms", "per_request_p50_ms",
+                                                             "per_request_p99_ms")}
+    cb = g("cpu_baseline")
+    if cb:
+        out["cpu_baseline_GBps"] = _r(cb["value"])
+    return out
 
 
 def main():
@@ -806,7 +901,8 @@ def main():
             ht = w.text if fm == A.AC_U8 else workloads.pack2(w.text)
             av = A.ac_build(w.patterns, alphabet="ACGT", num_subsets=K, device=dev)
             dt = torch.from_numpy(ht).to(f"cuda:{dev}")
-            tt, ss, mm = time_device_path(A, torch, av, dt, n, fm, max(3, args.steps // 4), 2, pg, stream)
+            tt, ss, mm = time_device_path(A, torch, av, dt, n, fm, max(3, args.steps // 4), 2, pg, stream,
+                                          prewarm_s=0.1)
             lk = K * n / max(1, A.ac_stats(av)["scan_stride"])  # dependent lookups per launch
             steps_v = max(3, args.steps // 4)
             var[f"K{K}-{f}"] = {"GBps": ht.size * steps_v / tt / 1e9, "symbols_per_s": n * steps_v / tt,
@@ -835,6 +931,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(w)
 
     if rank == 0:
+        line["summary"] = summary(line)  # last key: a short digest of every section
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -446,6 +446,15 @@ AC_API int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_
 AC_API int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt,
                     uint64_t *ticket);
 
+/* ac_serve_submit for a request that arrived before the call: arrival_ns is
+ * its arrival time on the host's monotonic clock (CLOCK_MONOTONIC, in ns;
+ * e.g. the moment a load generator scheduled it), and the server's latency
+ * statistics count from that time instead of from the call, so that time a
+ * request spent before reaching the server is not lost. Otherwise as
+ * ac_serve_submit. */
+AC_API int ac_serve_submit_at(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt,
+                              uint64_t arrival_ns, uint64_t *ticket);
+
 /* Non-blocking: AC_EAGAIN while pending; AC_OK moves the result into *out
  * (the ticket is then consumed). */
 AC_API int ac_serve_poll(ac_server *s, uint64_t ticket, ac_result *out);
@@ -453,6 +462,9 @@ AC_API int ac_serve_poll(ac_server *s, uint64_t ticket, ac_result *out);
 /* Blocking with a timeout in milliseconds: AC_ETIMEDOUT if not done in time. */
 AC_API int ac_serve_wait(ac_server *s, uint64_t ticket, uint32_t timeout_ms, ac_result *out);
 
+/* Counters of a server; p50_ms / p99_ms: latency percentiles of the
+ * completed requests, from arrival (the submit call, or the time given to
+ * ac_serve_submit_at) to the result on the host. */
 typedef struct {
     uint64_t submitted, completed, launches, items_launched, queued, in_flight;
     double p50_ms, p99_ms, mean_batch_items;

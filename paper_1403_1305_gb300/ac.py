@@ -33,7 +33,7 @@ AC_STAGE_DEVICE, AC_STAGE_PINNED = 0, 1
 
 EXPORTED = (
     "ac_build", "ac_free", "ac_save", "ac_load", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
-    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit",
+    "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit", "ac_serve_submit_at",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
     "ac_version", "ac_probe_gather",
 )
@@ -137,6 +137,7 @@ def _declare(lib):
         "ac_results_take": (C.c_int, [C.POINTER(ac_result), u32, vp, vp, vp, vp]),
         "ac_serve_create": (C.c_int, [C.POINTER(vp), u32, C.POINTER(ac_serve_opts), C.POINTER(vp)]),
         "ac_serve_submit": (C.c_int, [vp, u32, vp, u64, C.c_int, C.POINTER(u64)]),
+        "ac_serve_submit_at": (C.c_int, [vp, u32, vp, u64, C.c_int, u64, C.POINTER(u64)]),
         "ac_serve_poll": (C.c_int, [vp, u64, C.POINTER(ac_result)]),
         "ac_serve_wait": (C.c_int, [vp, u64, u32, C.POINTER(ac_result)]),
         "ac_serve_stats": (C.c_int, [vp, C.POINTER(ac_serve_stats_t)]),
@@ -477,6 +478,18 @@ def ac_serve_submit(s: Server, automaton: int, text, n: int | None = None, fmt: 
     nsym = int(n if n is not None else (nb if fmt == AC_U8 else 4 * nb))
     t = C.c_uint64()
     _check(lib().ac_serve_submit(s.h, automaton, ptr, nsym, fmt, C.byref(t)), "ac_serve_submit")
+    return int(t.value)
+
+
+def ac_serve_submit_at(s: Server, automaton: int, text, arrival_ns: int, n: int | None = None,
+                       fmt: int = AC_U8) -> int:
+    """:func:`ac_serve_submit` for a request that arrived at ``arrival_ns``
+    (``time.monotonic_ns()`` clock); latency statistics count from then."""
+    keep, ptr, nb = _host_bytes(text)
+    nsym = int(n if n is not None else (nb if fmt == AC_U8 else 4 * nb))
+    t = C.c_uint64()
+    _check(lib().ac_serve_submit_at(s.h, automaton, ptr, nsym, fmt, int(arrival_ns), C.byref(t)),
+           "ac_serve_submit_at")
     return int(t.value)
 
 

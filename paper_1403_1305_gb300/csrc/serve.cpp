@@ -36,7 +36,7 @@ struct Request {
     uint8_t *pinned = nullptr;  // copy in the page-locked slab, or
     std::vector<uint8_t> text;  // copy in ordinary host memory
     uint64_t slab_off = 0, slab_len = 0, staged_len = 0;
-    Clock::time_point t_submit;
+    Clock::time_point t_arrival;  // latency counts from here (submission, or the time the caller gave)
     const uint8_t *data() const { return staged ? staged : pinned ? pinned : text.data(); }
 };
 
@@ -186,7 +186,7 @@ void worker_loop(ac_server *s, int w) {
                 s->mem_in_use -= r->budget_bytes;
                 s->staged_bytes -= r->staged_len;
                 s->completed++;
-                s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+                s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_arrival).count());
                 if (r->pinned) s->slab.release(r->slab_off, r->slab_len);
                 delete r;
             }
@@ -279,7 +279,22 @@ int ac_serve_create(const ac_automaton *const *as, uint32_t na, const ac_serve_o
     return AC_OK;
 }
 
+static int submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt, uint64_t *ticket,
+                  Clock::time_point arrival);
+
 int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt, uint64_t *ticket) {
+    return submit(s, automaton, text, n, fmt, ticket, Clock::now());
+}
+
+int ac_serve_submit_at(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt,
+                       uint64_t arrival_ns, uint64_t *ticket) {
+    // steady_clock counts CLOCK_MONOTONIC nanoseconds on this platform
+    const Clock::time_point at{std::chrono::duration_cast<Clock::duration>(std::chrono::nanoseconds(arrival_ns))};
+    return submit(s, automaton, text, n, fmt, ticket, at);
+}
+
+static int submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint64_t n, int fmt, uint64_t *ticket,
+                  Clock::time_point arrival) {
     acgb::NvtxRange nvtx_range("ac_serve_submit");
     if (!s || !ticket || (!text && n)) return set_error(AC_EINVAL, "ac_serve_submit: NULL argument");
     if (automaton >= s->as.size()) return set_error(AC_EINVAL, "ac_serve_submit: no automaton %u", automaton);
@@ -296,7 +311,7 @@ int ac_serve_submit(ac_server *s, uint32_t automaton, const uint8_t *text, uint6
     r->fmt = fmt;
     r->n = n;
     r->budget_bytes = charge;
-    r->t_submit = Clock::now();
+    r->t_arrival = arrival;
     const uint64_t nbytes = fmt == AC_U8 ? n : (n + 3) / 4;
     bool to_device = false;
     {

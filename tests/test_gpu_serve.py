@@ -155,3 +155,23 @@ def test_unknown_staging(fleet):
     with pytest.raises(A.AcError) as e:
         A.ac_serve_create(autos, staging=2)
     assert e.value.code == A.AC_EINVAL
+
+
+def test_latency_counts_from_the_given_arrival(fleet):
+    """ac_serve_submit_at: a request that arrived 200 ms before it was
+    submitted is at least 200 ms late in the server's percentiles, and its
+    result is the same."""
+    import time
+    sets, autos, kinds, machines = fleet
+    rng = np.random.default_rng(64)
+    reqs = requests(rng, kinds, 8, lo=4096, hi=1 << 16)
+    srv = A.ac_serve_create(autos, num_streams=1)
+    past = time.monotonic_ns() - 200_000_000
+    tickets = [A.ac_serve_submit_at(srv, k, t, past) for k, t in reqs]
+    got = [A.ac_serve_wait(srv, tk, 60_000) for tk in tickets]
+    st = A.ac_serve_stats(srv)
+    A.ac_serve_destroy(srv)
+    assert st["p50_ms"] >= 200.0 and st["p99_ms"] < 60_000
+    for (k, t), (m, c) in zip(reqs, got):
+        wm, wc = machines[k].scan(t)
+        assert np.array_equal(m, wm) and np.array_equal(c, wc)
