@@ -156,12 +156,26 @@ struct ScanText {
     uint64_t row_begin = 0, row_end = 0;
 };
 
+// A stage of text whose walk is right but whose matches are still to be
+// emitted: the lean kernel walks such stages again, with their emission,
+// once the warp's row block is done instead of in the middle of it.
+struct EmitEntry {
+    uint32_t row;    // text row (0xffffffff: none)
+    uint32_t stage;  // stage index within the row's walk (warm-up stages first)
+    uint32_t s;      // state before the stage
+    uint32_t pad;
+};
+
 struct ScanOut {
     unsigned long long *keys;   // (pos << 32 | id), capacity `cap`
     uint64_t cap;
     unsigned long long *num;    // match counter (device)
     unsigned long long *counts; // per-pattern counts (device) or null
     uint32_t *err;              // device error word
+    // optional scratch of q_cap queue entries (lean kernel), split evenly between the launch's warps;
+    // null: stages with matches are walked again in place
+    EmitEntry *q = nullptr;
+    uint64_t q_cap = 0;
 };
 
 // Stage geometry shared by host planning and the kernels.

@@ -294,6 +294,14 @@ static int check_scan_args(const ac_automaton *a, uint64_t n, int fmt) {
 
 static uint64_t text_bytes(uint64_t n, int fmt) { return fmt == AC_U8 ? n : (n + 3) / 4; }
 
+// Entries of the lean kernel's queue of stages with matches (split evenly
+// between the launch's warps): one per 256 symbols and at least 65,536, at
+// most one per 16-byte stage; stages beyond a warp's part are walked again
+// in place, which is exact too.
+static uint64_t emit_queue_cap(uint64_t n, int fmt) {
+    return std::min<uint64_t>(text_bytes(n, fmt) / 16 + 1, n / 256 + 65536);
+}
+
 // Device copy of the text at a 16-byte aligned address. Texts shorter than
 // 64 bytes are copied into a zero-padded 64-byte buffer (the scan reads whole
 // 32-byte stages of full rows); *readable receives the bytes that may be read.
@@ -895,6 +903,13 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             cfg.row_len = (uint32_t)std::min<uint64_t>(rb * (fmt == AC_U8 ? 1 : 4), 1u << 20);
         }
         log_plan(a, n, fmt, cfg);
+        // the lean kernel hands stages with matches to a second kernel (not in the piecewise scan)
+        EmitEntry *q = nullptr;
+        uint64_t q_cap = 0;
+        if (!pipe && a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_LEAN) {
+            q_cap = emit_queue_cap(n, fmt);
+            q = (EmitEntry *)sc.get(q_cap * sizeof(EmitEntry));
+        }
         unsigned long long h_num[2];
         unsigned long long *keys = nullptr;
         for (int attempt = 0; attempt < 2; ++attempt) {
@@ -903,6 +918,10 @@ int ac_scan(const ac_automaton *a, const uint8_t *text, uint64_t n, int fmt, int
             CK(cudaMemsetAsync(num, 0, 16 + (size_t)a->P * 8, s), "ac_scan: memset");
             ScanText t{d_text, n, fmt, readable};
             ScanOut o{keys, cap, num, d_counts, err};
+            if (q) {
+                o.q = q;
+                o.q_cap = q_cap;
+            }
             if (pipe && attempt == 0)
                 e = pipelined_scan(a, text, d_text, t, o, cfg, s);
             else
@@ -981,11 +1000,19 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
     }
     // the short-text kernel has no device-side waits: no error word to check
     const bool waits = n && !(a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_SHORT);
+    // the lean kernel hands stages with matches to a second kernel through a queue
+    const bool lean = waits && a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_LEAN;
     uint32_t *err = nullptr;
+    EmitEntry *q = nullptr;
+    uint64_t q_cap = 0;
     if (waits) {
         err = (uint32_t *)sc.get(16);
         if (!err) return set_error(AC_ENOMEM, "ac_scan_keys_async: scratch");
         CK(cudaMemsetAsync(err, 0, 16, s), "ac_scan_keys_async: memset");
+        if (lean) {
+            q_cap = emit_queue_cap(n, fmt);
+            q = (EmitEntry *)sc.get(q_cap * sizeof(EmitEntry));  // none: stages are walked again in place
+        }
     }
     CK(cudaMemsetAsync(d_num, 0, 8, s), "ac_scan_keys_async: memset");
     if (d_counts) CK(cudaMemsetAsync(d_counts, 0, (size_t)a->P * 8, s), "ac_scan_keys_async: memset counts");
@@ -993,6 +1020,10 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
         ScanText tx{t, n, fmt, readable};
         ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
                   err};
+        if (q) {
+            o.q = q;
+            o.q_cap = q_cap;
+        }
         rc = launch_scan(a, tx, o, cfg, s);
         if (rc) return rc;
     }

@@ -647,6 +647,10 @@ static int launch_lean(const ac_automaton *a, const ScanText &t, const ScanOut &
         fn = plan.mode == kern::LEAN_SMEM32 ? kern::lean_u8_smem32(cfg.threads, cfg.chains)
                                             : kern::lean_u8_e16(cfg.threads, cfg.chains);
     if (!fn) return set_error(AC_EINVAL, "scan: no lean kernel for this configuration");
+    if (o.q && o.q_cap) {
+        p.q = o.q;
+        p.q_cap = o.q_cap;
+    }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
     int sms = 148;
@@ -703,8 +707,8 @@ static int launch_short(const ac_automaton *a, const ScanText &t, const ScanOut 
     const uint32_t words = (uint32_t)((warm_bytes + 15) / 16 + rb / 16);
     kern::ShortFn fn = t.fmt == AC_PACKED2 ? (plan.mode == kern::SHORT_FULL ? kern::short_packed_full(words)
                                                                             : kern::short_packed_e16(words))
-                                           : (plan.mode == kern::SHORT_FULL ? kern::short_u8_full(words)
-                                                                            : kern::short_u8_e16(words));
+                                           : (plan.mode == kern::SHORT_FULL ? kern::short_u8_full(words, a->dna_acgt)
+                                                                            : kern::short_u8_e16(words, a->dna_acgt));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
     fn<<<(unsigned)grid, threads, plan.smem, stream>>>(p);

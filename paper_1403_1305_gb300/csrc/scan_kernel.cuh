@@ -87,6 +87,8 @@ struct ScanParams {
     unsigned long long *counts;
     uint32_t *err;
     uint64_t wait_ns;       // limit of every bounded device-side wait; 0 gives up at the first wait
+    EmitEntry *q;           // lean kernel: scratch for the queue of stages to emit, split between warps
+    uint64_t q_cap;         // (null: stages with matches are walked again in place)
     // batch mode (several texts in one arena of whole rows)
     const BatchItemDev *items;  // sorted by first row
     const BatchTileDev *tiles;  // one per tile: machine and first row

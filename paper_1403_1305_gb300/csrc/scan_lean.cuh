@@ -205,6 +205,38 @@ __device__ __forceinline__ uint32_t lean_careful(uint32_t s_in, uint64_t row, in
     return sc;
 }
 
+// The matches of one queued stage per lane (has): the stage's 16 bytes (all
+// A/C/G/T or packed codes, every position inside the text and owned by its
+// row, at byte b0) walked again from s_in, emitting the output of every
+// flagged state through emit_warp. All 32 lanes call it together.
+template <int FMT, int LM>
+__device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_t b0, const ScanParams &p,
+                                                const SubsetDev &sd, const uint8_t *tab, uint32_t hot,
+                                                uint32_t lane) {
+    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;  // symbols per 32-bit word
+    uint32_t w[4] = {0, 0, 0, 0};
+    if (has) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.text + b0));  // 16-byte aligned
+        w[0] = (FMT == FMT_U8) ? acgt_codes4(v.x) : v.x;
+        w[1] = (FMT == FMT_U8) ? acgt_codes4(v.y) : v.y;
+        w[2] = (FMT == FMT_U8) ? acgt_codes4(v.z) : v.z;
+        w[3] = (FMT == FMT_U8) ? acgt_codes4(v.w) : v.w;
+    }
+    const uint64_t pol = l2_evict_last();
+    const uint64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
+    uint32_t sc = s_in;
+#pragma unroll 1
+    for (int e = 0; e < 4; ++e) {
+#pragma unroll 4
+        for (int b = 0; b < PER; ++b) {
+            const uint32_t c = (FMT == FMT_U8) ? (w[e] >> (8 * b)) & 3u : (w[e] >> (2 * b)) & 3u;
+            const uint32_t nv = has ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
+            sc = nv & kStateMask;
+            emit_warp((nv & kFlag) != 0, sc, pos0 + (uint64_t)(e * PER + b), 0, sd, p, lane);
+        }
+    }
+}
+
 // symbol code of 2-bit packed symbol b of word w, times 2 (E16) or 4 (SMEM32)
 template <int SH>
 __device__ __forceinline__ uint32_t packed_code(uint32_t w, int b) {
@@ -369,6 +401,10 @@ __global__ void __launch_bounds__(NT, 1)
         advance();
         const uint32_t rd = my_stage + lane * BX;  // this lane's row in each chain group's box
 
+        // this warp's part of the queue of stages whose matches are emitted after the row block
+        uint32_t qcount = 0;
+        const uint32_t qper = p.q ? (uint32_t)(p.q_cap / ((uint64_t)gridDim.x * nwarps)) : 0u;
+        EmitEntry *myq = p.q ? p.q + ((uint64_t)blockIdx.x * nwarps + warp) * qper : nullptr;
         uint32_t st[C];  // state per chain: SMEM32 row offset (| output bit), E16 id (| kFlag)
 #pragma unroll
         for (int j = 0; j < C; ++j) st[j] = 0;
@@ -444,19 +480,51 @@ __global__ void __launch_bounds__(NT, 1)
             }
             // Common case: every chain of the warp inside the text and one vote
             // finds no lane with an output or a byte outside ACGT.
-            bool slow = true;
+            bool slow = true, emit_only = false;
             if (s >= s_lo && s < s_hi) {
-                uint32_t flags = bad;
+                uint32_t flags = 0;
                 if (main_stage) {
 #pragma unroll
                     for (int j = 0; j < C; ++j) flags |= acc[j] & FLAG;
                 }
-                slow = __any_sync(kFull, flags != 0);
+                slow = __any_sync(kFull, (flags | bad) != 0);
+                // with a queue, a stage whose only reason to stop is an output
+                // keeps its states and hands its matches to the emitting kernel
+                emit_only = slow && p.q != nullptr && !__any_sync(kFull, bad != 0);
+            }
+            if (emit_only) {
+                // the warp's flagged chain stages go to its own part of the queue,
+                // walked again with their emission once the row block is done; a
+                // part too full for them leaves the stage to the careful walk
+                uint32_t total = 0;
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    total += __popc(__ballot_sync(kFull, (acc[j] & FLAG) != 0 && row0 + (uint64_t)j * 32 + lane < p.row_end));
+                if (qcount + total <= qper) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        const bool f = (acc[j] & FLAG) != 0 && row0 + (uint64_t)j * 32 + lane < p.row_end;
+                        const unsigned bal = __ballot_sync(kFull, f);
+                        if (f) {
+                            EmitEntry en;
+                            en.row = (uint32_t)(row0 + (uint64_t)j * 32 + lane);
+                            en.stage = s;
+                            en.s = LM == LEAN_SMEM32 ? (st[j] >> 4) : (st[j] & kStateMask);
+                            en.pad = 0;
+                            myq[qcount + __popc(bal & ((1u << lane) - 1u))] = en;
+                        }
+                        qcount += __popc(bal);
+                    }
+#pragma unroll
+                    for (int j = 0; j < C; ++j) st[j] = u[j];
+                } else {
+                    emit_only = false;  // the careful walk below
+                }
             }
             if (!slow) {
 #pragma unroll
                 for (int j = 0; j < C; ++j) st[j] = u[j];
-            } else {
+            } else if (!emit_only) {
                 // chain by chain (a rolled loop over a rotation of the per-chain
                 // registers, so the careful walk is inlined once): positions,
                 // then a careful walk wherever a lane of the chain needs one
@@ -487,6 +555,17 @@ __global__ void __launch_bounds__(NT, 1)
                     st[C - 1] = nx;
                 }
             }
+        }
+        // the queued stages of this row block, walked again with their emission
+        // (a lane per stage; its bytes are read again from global memory)
+#pragma unroll 1
+        for (uint32_t i = 0; i < qcount; i += 32) {
+            EmitEntry en{0xffffffffu, 0, 0, 0};
+            if (i + lane < qcount) en = myq[i + lane];
+            const bool has = en.row != 0xffffffffu;
+            const int64_t o = ((int64_t)en.stage - (int64_t)nW) * BX;
+            lean_emit_stage<FMT, LM>(has, en.s, has ? (uint64_t)((int64_t)en.row * L32 + o) : 0, p, *sdp, tab, hot,
+                                     lane);
         }
     };
 

@@ -51,8 +51,73 @@ __device__ __forceinline__ uint32_t short_step(uint32_t s, uint32_t c, const uin
     return nv;
 }
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// E16 lookup (as the lean kernel's): the 16-bit prefix entry at shared
+// address sa when s < hot and it is not the escape, else the 32-bit table
+// entry at byte offset 2 * gi.
+__device__ __forceinline__ uint32_t short_e16(uint32_t s, uint32_t sa, uint32_t gi, uint32_t hot,
+                                              const uint32_t *gtab) {
+    uint32_t e;
+    asm("{\n\t.reg .pred ps, pg;\n\t.reg .u64 ga;\n\t"
+        "setp.lt.u32 ps, %1, %3;\n\t"
+        "mov.u32 %0, 65535;\n\t"
+        "@ps ld.shared.u16 %0, [%2];\n\t"
+        "setp.eq.u32 pg, %0, 65535;\n\t"
+        "mad.wide.u32 ga, %4, 2, %5;\n\t"
+        "@pg ld.global.nc.u32 %0, [ga];\n\t}"
+        : "=r"(e)
+        : "r"(s), "r"(sa), "r"(hot), "r"(gi), "l"(gtab));
+    return e;
+}
+
+// One 16-byte word of symbols walked without any per-symbol check: every
+// symbol lies inside the text and in the alphabet (ACGT bytes, or packed
+// codes). FULL: the 32-bit table, entry at byte (s << 4) + 4c; E16: the
+// 16-bit prefix (byte (s << 3) + 2c) and the 32-bit table beyond it. The
+// state is updated in place; returns the OR of the entries (output flags).
+template <int FMT, int SM>
+__device__ __forceinline__ uint32_t short_fast_word(const uint4 &v, uint32_t &s, uint32_t sbase, uint32_t hot,
+                                                    const uint32_t *gtab) {
+    constexpr uint32_t SH = (SM == SHORT_FULL) ? 2 : 1;  // code -> byte offset in the row
+    uint32_t acc = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t x = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+        constexpr int PER = (FMT == FMT_U8) ? 4 : 16;
+        const uint32_t cw = (FMT == FMT_U8) ? (acgt_codes4(x) << SH) : x;
+#pragma unroll
+        for (int b = 0; b < PER; ++b) {
+            uint32_t off;  // code << SH
+            if (FMT == FMT_U8) off = __byte_perm(cw, 0, 0x4440 + b);
+            else off = ((2 * b >= (int)SH) ? (cw >> (2 * b - SH)) : (cw << (SH - 2 * b))) & (3u << SH);
+            uint32_t nv;
+            if (SM == SHORT_FULL) {
+                nv = lds_u32(sbase + (s << 4) + off);
+            } else {
+                const uint32_t gi = (s << 3) + off;
+                nv = short_e16(s, sbase + gi, gi, hot, gtab);
+            }
+            acc |= nv;
+            s = nv & kStateMask;
+        }
+    }
+    return acc;
+}
+
+// all 16 bytes of the word are A, C, G or T
+__device__ __forceinline__ bool word_is_acgt(const uint4 &v) {
+    return (acgt_mismatch4(v.x, acgt_codes4(v.x)) | acgt_mismatch4(v.y, acgt_codes4(v.y)) |
+            acgt_mismatch4(v.z, acgt_codes4(v.z)) | acgt_mismatch4(v.w, acgt_codes4(v.w))) == 0;
+}
+
 // MAXW: words of the window a thread holds (warm-up + row words <= MAXW).
-template <int FMT, int SM, int MAXW>
+// ACGT: byte text over exactly A, C, G, T (decoded without the symbol map).
+template <int FMT, int SM, int MAXW, bool ACGT>
 __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ ScanParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const SubsetDev &sd = *p.subs;
@@ -121,16 +186,24 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
         const int64_t pos0 = (b0 + 16 * (int64_t)k) * (SYM / 16);
         const uint32_t s_in = s;
         uint32_t acc = 0;
-        // 16 symbols per inner pass: one pass for bytes, four for packed text
+        // a word wholly inside the text (and, for bytes, wholly A/C/G/T) is
+        // walked without per-symbol checks
+        const bool fast = active && pos0 >= 0 && pos0 + (int64_t)SYM <= nsym &&
+                          (FMT == FMT_P2 || (ACGT && word_is_acgt(cur)));
+        if (fast) {
+            acc = short_fast_word<FMT, SM>(cur, s, smem_addr(tab), hot, sd.table);
+        } else {
+            // 16 symbols per inner pass: one pass for bytes, four for packed text
 #pragma unroll 1
-        for (uint32_t q = 0; q < SYM; q += 16) {
+            for (uint32_t q = 0; q < SYM; q += 16) {
 #pragma unroll
-            for (uint32_t i = 0; i < 16; ++i) {
-                const int64_t pos = pos0 + q + i;
-                const uint32_t nv = short_step<SM>(s, word_symbol<FMT>(cur, q + i, smap), tab, hot, sd.table);
-                const bool live = active && pos >= 0 && pos < nsym;
-                s = live ? (nv & kStateMask) : 0u;
-                acc |= live ? nv : 0u;
+                for (uint32_t i = 0; i < 16; ++i) {
+                    const int64_t pos = pos0 + q + i;
+                    const uint32_t nv = short_step<SM>(s, word_symbol<FMT>(cur, q + i, smap), tab, hot, sd.table);
+                    const bool live = active && pos >= 0 && pos < nsym;
+                    s = live ? (nv & kStateMask) : 0u;
+                    acc |= live ? nv : 0u;
+                }
             }
         }
         if (k >= nw_warm && __any_sync(kFull, (acc & kFlag) != 0)) {
@@ -147,15 +220,19 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
     }
 }
 
-template <int FMT, int SM>
+template <int FMT, int SM, bool ACGT>
 ShortFn pick_short(uint32_t words) {
-    return words <= 5 ? short_kernel<FMT, SM, 5> : short_kernel<FMT, SM, kShortMaxWords>;
+    return words <= 5 ? short_kernel<FMT, SM, 5, ACGT> : short_kernel<FMT, SM, kShortMaxWords, ACGT>;
 }
 
-ShortFn short_u8_full(uint32_t words) { return pick_short<FMT_U8, SHORT_FULL>(words); }
-ShortFn short_u8_e16(uint32_t words) { return pick_short<FMT_U8, SHORT_E16>(words); }
-ShortFn short_packed_full(uint32_t words) { return pick_short<FMT_P2, SHORT_FULL>(words); }
-ShortFn short_packed_e16(uint32_t words) { return pick_short<FMT_P2, SHORT_E16>(words); }
+ShortFn short_u8_full(uint32_t words, bool acgt) {
+    return acgt ? pick_short<FMT_U8, SHORT_FULL, true>(words) : pick_short<FMT_U8, SHORT_FULL, false>(words);
+}
+ShortFn short_u8_e16(uint32_t words, bool acgt) {
+    return acgt ? pick_short<FMT_U8, SHORT_E16, true>(words) : pick_short<FMT_U8, SHORT_E16, false>(words);
+}
+ShortFn short_packed_full(uint32_t words) { return pick_short<FMT_P2, SHORT_FULL, false>(words); }
+ShortFn short_packed_e16(uint32_t words) { return pick_short<FMT_P2, SHORT_E16, false>(words); }
 
 }  // namespace kern
 }  // namespace acgb
