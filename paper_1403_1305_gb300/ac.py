@@ -425,22 +425,40 @@ def ac_scan_noalloc(a: Automaton, d_text, n: int, fmt: int, stream, d_matches, c
     _check(rc, "ac_scan_noalloc")
 
 
+_ITEM_DTYPE = np.dtype({"names": ["automaton", "fmt", "text", "n"], "formats": [np.uint32, np.int32, np.uint64, np.uint64],
+                        "offsets": [ac_batch_item.automaton.offset, ac_batch_item.fmt.offset,
+                                    ac_batch_item.text.offset, ac_batch_item.n.offset],
+                        "itemsize": C.sizeof(ac_batch_item)})
+
+
 def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=None):
     """``items``: list of ``(automaton_index, text, n, fmt)``; texts are host
     buffers (mem=AC_HOST) or CUDA tensors (mem=AC_DEVICE). Returns a list of
     ``(matches, counts)`` (counts None with AC_BATCH_NO_COUNTS)."""
     hs = (C.c_void_p * max(1, len(automata)))(*[a.h for a in automata])
-    arr = (ac_batch_item * max(1, len(items)))()
+    # the item array filled column by column (one ctypes struct per item costs microseconds each)
+    arr = np.zeros(max(1, len(items)), dtype=_ITEM_DTYPE)
     keep = []
-    for i, (ai, text, n, fmt) in enumerate(items):
+    if items:
+        ai, texts, ns, fmts = zip(*items)
         if mem == AC_DEVICE:
-            ptr = _device_ptr(text)
+            for t in texts:
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("device texts must be contiguous CUDA tensors")
+            ptrs = [t.data_ptr() for t in texts]
         else:
-            k, ptr, _ = _host_bytes(text)
-            keep.append(k)
-        arr[i] = ac_batch_item(int(ai), int(fmt), ptr, int(n))
+            ptrs = []
+            for t in texts:
+                k, ptr, _ = _host_bytes(t)
+                keep.append(k)
+                ptrs.append(ptr.value or 0)
+        arr["automaton"][:len(items)] = ai
+        arr["fmt"][:len(items)] = fmts
+        arr["text"][:len(items)] = ptrs
+        arr["n"][:len(items)] = ns
+    arr_p = arr.ctypes.data_as(C.POINTER(ac_batch_item))
     outs = (ac_result * max(1, len(items)))()
-    _check(lib().ac_scan_batch(hs, len(automata), arr, len(items), mem, int(flags), _stream_ptr(stream), outs),
+    _check(lib().ac_scan_batch(hs, len(automata), arr_p, len(items), mem, int(flags), _stream_ptr(stream), outs),
            "ac_scan_batch")
     return _take_results(outs, len(items), not (flags & AC_BATCH_NO_COUNTS))
 

@@ -1000,7 +1000,7 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
     }
     // the short-text kernel has no device-side waits: no error word to check
     const bool waits = n && !(a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_SHORT);
-    // the lean kernel hands stages with matches to a second kernel through a queue
+    // the lean kernel queues stages with matches and walks them after each row block
     const bool lean = waits && a->machine == AC_MACHINE_DFA && cfg.kernel == AC_KERNEL_LEAN;
     uint32_t *err = nullptr;
     EmitEntry *q = nullptr;
@@ -1008,14 +1008,15 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
     if (waits) {
         err = (uint32_t *)sc.get(16);
         if (!err) return set_error(AC_ENOMEM, "ac_scan_keys_async: scratch");
-        CK(cudaMemsetAsync(err, 0, 16, s), "ac_scan_keys_async: memset");
         if (lean) {
             q_cap = emit_queue_cap(n, fmt);
             q = (EmitEntry *)sc.get(q_cap * sizeof(EmitEntry));  // none: stages are walked again in place
         }
     }
-    CK(cudaMemsetAsync(d_num, 0, 8, s), "ac_scan_keys_async: memset");
-    if (d_counts) CK(cudaMemsetAsync(d_counts, 0, (size_t)a->P * 8, s), "ac_scan_keys_async: memset counts");
+    // error word, counter and counts zeroed by one launch
+    rc = launch_zero((unsigned long long *)err, err ? 2 : 0, (unsigned long long *)d_num, 1,
+                     (unsigned long long *)d_counts, d_counts ? a->P : 0, s);
+    if (rc) return rc;
     if (n) {
         ScanText tx{t, n, fmt, readable};
         ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,

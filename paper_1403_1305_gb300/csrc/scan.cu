@@ -19,6 +19,16 @@ __global__ void fill_u64_kernel(unsigned long long *p, uint64_t count, unsigned 
         p[i] = value;
 }
 
+__global__ void zero3_kernel(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1,
+                             unsigned long long *p2, uint64_t n2) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n0 + n1 + n2; i += stride) {
+        if (i < n0) p0[i] = 0;
+        else if (i < n0 + n1) p1[i - n0] = 0;
+        else p2[i - n0 - n1] = 0;
+    }
+}
+
 __global__ void keys_to_matches_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num,
                                        uint64_t cap, uint32_t shift, ac_match *__restrict__ out,
                                        unsigned long long *num_out, const uint32_t *err) {
@@ -811,6 +821,16 @@ int launch_fill_u64(unsigned long long *ptr, uint64_t count, unsigned long long 
     fill_u64_kernel<<<(unsigned)blocks, 256, 0, stream>>>(ptr, count, value);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "fill: %s", cudaGetErrorString(e));
+}
+
+int launch_zero(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1, unsigned long long *p2,
+                uint64_t n2, cudaStream_t stream) {
+    const uint64_t total = n0 + n1 + n2;
+    if (!total) return AC_OK;
+    const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 1024);
+    zero3_kernel<<<(unsigned)blocks, 256, 0, stream>>>(p0, n0, p1, n1, p2, n2);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "zero: %s", cudaGetErrorString(e));
 }
 
 int launch_keys_to_matches(const unsigned long long *keys, const unsigned long long *num, uint64_t cap,
