@@ -224,8 +224,8 @@ typedef struct {
                                (placement AUTO, SMEM or HYBRID16): the whole table in shared memory when it
                                fits, else an escape-coded 16-bit breadth-first prefix with the rest read
                                through L2; 16-byte stages; (threads, chains) in {(1024, 4), (1024, 2),
-                               (768, 4), (512, 4)}, default (1024, 4). AC_EINVAL at scan time when it does
-                               not apply. */
+                               (768, 4), (512, 4)}, default (1024, 2) for byte text and (1024, 4) for
+                               packed text. AC_EINVAL at scan time when it does not apply. */
 #define AC_KERNEL_SHORT 3   /* short texts on one 4-letter machine (one subset, any 4-letter alphabet, u8 or
                                packed text, placement AUTO, SMEM or HYBRID16): one thread per row of 16 to 64
                                bytes (row_len; by default about 150,000 rows: 16 bytes up to 2.4 MB of text,

@@ -346,18 +346,21 @@ __global__ void __launch_bounds__(NT, 1)
         const uint32_t nW = (warm_bytes + BX - 1) / BX;
         const uint32_t L32 = p.row_bytes;
         const uint32_t nst = nW + L32 / BX;
-        // The partial last row of the text (if any) is read from global memory
-        // by the careful walk at every stage (its bytes beyond the text end are
-        // not in the row tensor map).
-        const bool tail_in_warp =
-            p.tail_bytes && p.full_rows >= row0 && p.full_rows < row0 + 32 * C && p.full_rows < p.row_end;
+        // Rows at or beyond full_rows (the partial last row, and rows past the
+        // end of the text in the last row block) are not in the row tensor map:
+        // their boxes are zero-filled or not copied. After each stage lands,
+        // their lanes write their 16 bytes into the slot themselves -- the
+        // partial last row its own bytes (read from global memory), the others
+        // a filler of A codes whose walk is thrown away -- so that the fast
+        // loop sees only letters of the alphabet.
+        const bool has_oob = row0 + 32 * C > p.full_rows;
         // Stages [s_lo, s_hi) have every row of the warp inside the text (no
-        // text edge, no partial row): their stages need no per-chain checks.
+        // text edge): their stages need no per-chain checks.
         const uint64_t row_last = min(row0 + 32 * C, p.row_end) - 1;
         const uint64_t warm_total = (uint64_t)nW * BX;
         const uint32_t s_lo = row0 * L32 >= warm_total ? 0u : (uint32_t)(nW - row0 * L32 / BX);
         uint32_t s_hi = 0;
-        if (!tail_in_warp) {
+        {
             const int64_t spb = (FMT == FMT_U8) ? 1 : 4;
             const int64_t lim = ((int64_t)p.nsym - (int64_t)SYM) / spb - (int64_t)row_last * L32;  // max stage byte offset
             if (p.nsym >= SYM && lim >= -(int64_t)warm_total) {
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
         };
         // a warp whose rows are all beyond the full rows (only the partial last
-        // row) has nothing to copy: its stages are all walked carefully
+        // row) has nothing to copy: its lanes fill the slot themselves (above)
         const bool copies = bytes != 0;
         if (copies && lane == 0) issue();
         advance();
@@ -416,6 +419,38 @@ __global__ void __launch_bounds__(NT, 1)
                     return;
                 }
                 parity ^= 1u;
+            }
+            if (has_oob) {
+                const int64_t o = ((int64_t)s - (int64_t)nW) * BX;  // stage offset from the row start
+                constexpr uint32_t kFill = (FMT == FMT_U8) ? 0x41414141u : 0u;  // "AAAA" (code 0)
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const uint64_t row = row0 + (uint64_t)j * 32 + lane;
+                    if (row >= p.full_rows) {
+                        uint32_t v[4] = {kFill, kFill, kFill, kFill};
+                        if (row == p.full_rows && row < p.row_end) {
+                            // the partial last row (its box may not have been copied at all: its
+                            // warm-up too); bytes outside the text stay filler
+                            const int64_t b0 = (int64_t)row * L32 + o;
+                            if (b0 >= 0 && b0 + 16 <= (int64_t)p.nbytes) {
+                                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p.text + b0));  // 16-byte aligned
+                                v[0] = x.x;
+                                v[1] = x.y;
+                                v[2] = x.z;
+                                v[3] = x.w;
+                            } else {
+                                for (int k = 0; k < 16; ++k)
+                                    if (b0 + k >= 0 && b0 + k < (int64_t)p.nbytes)
+                                        v[k >> 2] = (v[k >> 2] & ~(0xffu << (8 * (k & 3)))) |
+                                                    ((uint32_t)__ldg(p.text + b0 + k) << (8 * (k & 3)));
+                            }
+                        }
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(rd + j * BOX), "r"(v[0]),
+                                     "r"(v[1]), "r"(v[2]), "r"(v[3])
+                                     : "memory");
+                    }
+                }
+                __syncwarp();
             }
             const bool main_stage = s >= nW;
             uint32_t u[C], acc[C], bad = 0;  // bad: bytes outside ACGT in any chain of the thread
@@ -536,7 +571,9 @@ __global__ void __launch_bounds__(NT, 1)
                     const int64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
                     const bool dead = row >= p.row_end || pos0 >= nsym;
                     const bool before = !dead && pos0 + (int64_t)SYM <= 0;
-                    const bool fast = !dead && pos0 >= 0 && pos0 + (int64_t)SYM <= nsym && row < p.full_rows;
+                    // (the partial last row's stages were written into the slot: its stages inside the
+                    // text are as good as any)
+                    const bool fast = !dead && pos0 >= 0 && pos0 + (int64_t)SYM <= nsym;
                     const bool need = !dead && !before && (!fast || bad != 0 || (main_stage && (acc[0] & FLAG)));
                     uint32_t nx = u[0];
                     if (__any_sync(kFull, need)) {
