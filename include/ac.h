@@ -202,7 +202,8 @@ typedef struct {
                              for the short-text kernel) */
     uint32_t threads;     /* threads per CTA (multiple of 32; <= 512 for the general kernel; 512, 768 or
                              1024 for the lean one; 64 to 1024 for the short-text one) */
-    uint32_t chains;      /* independent chains per thread: 1, 2 or 4 (1 for the short-text kernel) */
+    uint32_t chains;      /* independent chains per thread: 1, 2 or 4 (3 too for the lean kernel; 1 for the
+                             short-text kernel) */
     uint32_t ctas;        /* persistent grid size; 0 = one per SM */
     uint32_t stage_bytes; /* text bytes per chain per pipeline stage: 16 or 32 (16 needs 2 or 4 chains; the
                              lean kernel always uses 16) */
@@ -223,9 +224,9 @@ typedef struct {
 #define AC_KERNEL_LEAN 2    /* one-symbol scans of a 4-letter machine over ACGT bytes or packed text
                                (placement AUTO, SMEM or HYBRID16): the whole table in shared memory when it
                                fits, else an escape-coded 16-bit breadth-first prefix with the rest read
-                               through L2; 16-byte stages; (threads, chains) in {(1024, 4), (1024, 2),
-                               (768, 4), (512, 4)}, default (1024, 2) for byte text and (1024, 4) for
-                               packed text. AC_EINVAL at scan time when it does not apply. */
+                               through L2; 16-byte stages; (threads, chains) in {(1024, 4), (1024, 3),
+                               (1024, 2), (768, 4), (512, 4)}, default (1024, 2) for byte text and
+                               (1024, 3) for packed text. AC_EINVAL at scan time when it does not apply. */
 #define AC_KERNEL_SHORT 3   /* short texts on one 4-letter machine (one subset, any 4-letter alphabet, u8 or
                                packed text, placement AUTO, SMEM or HYBRID16): one thread per row of 16 to 64
                                bytes (row_len; by default about 150,000 rows: 16 bytes up to 2.4 MB of text,

@@ -790,8 +790,8 @@ int ac_set_scan_config(ac_automaton *a, const ac_scan_config *cfg) {
     if (!a || !cfg) return set_error(AC_EINVAL, "ac_set_scan_config: NULL argument");
     if (cfg->threads && (cfg->threads % 32 || cfg->threads > 1024))
         return set_error(AC_EINVAL, "ac_set_scan_config: threads must be a multiple of 32, at most 1024");
-    if (cfg->chains && cfg->chains != 1 && cfg->chains != 2 && cfg->chains != 4)
-        return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4");
+    if (cfg->chains && (cfg->chains > 4 || (cfg->chains == 3 && cfg->kernel != AC_KERNEL_LEAN)))
+        return set_error(AC_EINVAL, "ac_set_scan_config: chains must be 1, 2 or 4 (3 with the lean kernel)");
     if (cfg->kernel > AC_KERNEL_SHORT) return set_error(AC_EINVAL, "ac_set_scan_config: unknown kernel %u", cfg->kernel);
     if (cfg->stage_bytes && cfg->stage_bytes != 16 && cfg->stage_bytes != 32)
         return set_error(AC_EINVAL, "ac_set_scan_config: stage bytes must be 16 or 32");

@@ -168,7 +168,7 @@ uint64_t scan_row_bytes(const ac_scan_config &cfg, int fmt, uint64_t readable) {
 
 // ------------------------------------------------------------------ lean kernel
 bool lean_shape_ok(uint32_t threads, uint32_t chains) {
-    return (threads == 1024 && (chains == 4 || chains == 2)) || (threads == 768 && chains == 4) ||
+    return (threads == 1024 && (chains == 4 || chains == 3 || chains == 2)) || (threads == 768 && chains == 4) ||
            (threads == 512 && chains == 4);
 }
 
@@ -183,8 +183,9 @@ const char *lean_unfit(const ac_automaton *a, const ac_scan_config &c, int fmt) 
         return "it supports placements AUTO, SMEM and HYBRID16";
     if (c.stage_bytes && c.stage_bytes != kern::kLeanBX) return "it uses 16-byte stages";
     const uint32_t t = c.threads ? c.threads : 1024;
-    const uint32_t ch = c.chains ? c.chains : (fmt == AC_U8 ? 2u : 4u);
-    if (!lean_shape_ok(t, ch)) return "(threads, chains) must be (1024, 4), (1024, 2), (768, 4) or (512, 4)";
+    const uint32_t ch = c.chains ? c.chains : (fmt == AC_U8 ? 2u : 3u);
+    if (!lean_shape_ok(t, ch))
+        return "(threads, chains) must be (1024, 4), (1024, 3), (1024, 2), (768, 4) or (512, 4)";
     uint32_t max_states = 0;
     for (auto &d : a->h_desc) {
         if (d.states >= (1u << 28)) return "it needs fewer than 2^28 states per subset";
@@ -286,10 +287,10 @@ static void fill_config(const ac_automaton *a, ac_scan_config c, uint64_t n, int
     if (lean_ok) {
         c.kernel = AC_KERNEL_LEAN;
         if (!c.threads) c.threads = 1024;
-        // byte text: 2 chains per thread (the row block ends sooner and the
-        // shared-memory prefix is larger); packed text: 4 (a 16-byte stage
-        // is 64 symbols, so more chains keep more lookups in flight)
-        if (!c.chains) c.chains = fmt == AC_U8 ? 2 : 4;
+        // byte text: 2 chains per thread (less staging, so a larger shared-
+        // memory prefix, and the row block ends sooner); packed text: 3 (a
+        // 16-byte stage is 64 symbols)
+        if (!c.chains) c.chains = fmt == AC_U8 ? 2 : 3;
         c.stage_bytes = kern::kLeanBX;
         if (!c.row_len) {
             int sms = 148;

@@ -663,6 +663,7 @@ template <int FMT, int LM>
 LeanFn pick_lean_shape(uint32_t threads, uint32_t C) {
     if (threads == 1024) {
         if (C == 4) return lean_kernel<FMT, LM, 4, 1024>;
+        if (C == 3) return lean_kernel<FMT, LM, 3, 1024>;
         if (C == 2) return lean_kernel<FMT, LM, 2, 1024>;
     } else if (threads == 768 && C == 4) {
         return lean_kernel<FMT, LM, 4, 768>;

@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 
 THREADS = os.cpu_count() or 4
 ACGT = np.frombuffer(b"ACGT", np.uint8)
-SHAPES = [(1024, 4), (1024, 2), (768, 4), (512, 4)]
+SHAPES = [(1024, 4), (1024, 3), (1024, 2), (768, 4), (512, 4)]
 
 
 @pytest.fixture(scope="module", autouse=True)
