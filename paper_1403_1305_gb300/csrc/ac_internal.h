@@ -196,6 +196,8 @@ uint32_t scan_stage_bytes_per_cta(const ac_scan_config &cfg);
 void default_config(const ac_automaton *a, uint64_t n, int fmt, ac_scan_config *cfg);
 int launch_scan(const ac_automaton *a, const ScanText &t, const ScanOut &o, const ac_scan_config &cfg,
                 cudaStream_t stream);
+// entries of the lean kernel's emission queue for a text of n symbols (capi.cu)
+uint64_t emit_queue_cap(uint64_t n, int fmt);
 // Table placement and symbols per lookup of a single-text scan (format fmt)
 // under configuration cfg (defaults filled in): kernel mode (the kernels'
 // MODE_* values), table rows staged in shared memory, words of shared memory

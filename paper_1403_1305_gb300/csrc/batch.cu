@@ -479,6 +479,8 @@ struct Segment {
     uint8_t *buf = nullptr;
     unsigned long long *keys = nullptr;
     uint64_t cap = 0;
+    EmitEntry *q = nullptr;  // lean kernel's emission queue
+    uint64_t q_cap = 0;
 };
 
 int scan_segments(const ac_automaton *const *as, const ac_batch_item *items, const std::vector<uint32_t> &idx,
@@ -562,6 +564,17 @@ int scan_segments(const ac_automaton *const *as, const ac_batch_item *items, con
             default_config(sg.a, sg.len, AC_U8, &cfg);
             ScanText t{sg.buf, sg.len, AC_U8, sg.alloc};
             ScanOut o{sg.keys, sg.cap, d_ctr + 2 * g, nullptr, (uint32_t *)(d_ctr + 2 * g + 1)};
+            if (cfg.kernel == AC_KERNEL_LEAN && sg.a->machine == AC_MACHINE_DFA) {
+                // the lean kernel's emission queue (none: stages with matches are walked again in place)
+                if (!sg.q) {
+                    sg.q_cap = emit_queue_cap(sg.len, AC_U8);
+                    sg.q = (EmitEntry *)pool.get(sg.q_cap * sizeof(EmitEntry));
+                }
+                if (sg.q) {
+                    o.q = sg.q;
+                    o.q_cap = sg.q_cap;
+                }
+            }
             const int rc = launch_scan(sg.a, t, o, cfg, s);
             if (rc) return rc;
         }

@@ -298,7 +298,7 @@ static uint64_t text_bytes(uint64_t n, int fmt) { return fmt == AC_U8 ? n : (n +
 // between the launch's warps): one per 256 symbols and at least 65,536, at
 // most one per 16-byte stage; stages beyond a warp's part are walked again
 // in place, which is exact too.
-static uint64_t emit_queue_cap(uint64_t n, int fmt) {
+uint64_t emit_queue_cap(uint64_t n, int fmt) {
     return std::min<uint64_t>(text_bytes(n, fmt) / 16 + 1, n / 256 + 65536);
 }
 
