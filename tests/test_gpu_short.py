@@ -192,3 +192,35 @@ def test_refusals():
     with pytest.raises(A.AcError) as e:
         A.ac_scan(p, b"ACDWY")
     assert e.value.code == A.AC_EINVAL
+
+
+def async_scan(a, d_text, n, cap, fmt=A.AC_U8):
+    d_m = torch.full((2 * max(cap, 1),), -1, dtype=torch.int32, device="cuda")
+    d_num = torch.full((1,), 777, dtype=torch.int64, device="cuda")
+    d_c = torch.full((a.num_patterns,), 5, dtype=torch.int64, device="cuda")
+    A.ac_scan_async(a, d_text, n, fmt, None, d_m, cap, d_num, d_c)
+    torch.cuda.synchronize()
+    M = int(d_num.item())
+    return M, d_m.view(-1, 2)[:min(M, cap)].cpu().numpy().view(np.uint32), d_c.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("placement", ["full", "e16"])
+def test_async_small_capacities(placement):
+    """ac_scan_async on short texts with capacities of 1..2,048 records
+    (the rank sort), results of 0..~1,900 matches, packed and byte text;
+    with M > cap the count and the counts are still exact."""
+    rng = np.random.default_rng(1700 + (placement == "e16"))
+    for i, (n, P, cap) in enumerate(((20_000, 40, 2048), (50_000, 300, 1024), (3_000, 10, 64), (120_000, 200, 2048),
+                                     (1, 5, 1), (700_000, 100, 2048), (9_000, 60, 7))):
+        text = workloads.dna_text(rng, n)
+        pats = workloads.draw_patterns(rng, text, P, 4 if i % 2 else 6, 16, 0.9, ACGT)
+        kw = dict(placement=A.AC_PLACE_HYBRID16, smem_table_bytes=512) if placement == "e16" else {}
+        a = A.ac_build(pats, alphabet="ACGT", **kw)
+        assert A.ac_stats(a)["scan_kernel"] in (A.AC_KERNEL_SHORT, A.AC_KERNEL_LEAN)
+        wm, wc = oracle.scan(pats, text)
+        for fmt, t in ((A.AC_U8, text), (A.AC_PACKED2, workloads.pack2(text))):
+            M, m, c = async_scan(a, torch.from_numpy(np.ascontiguousarray(t)).cuda(), n, cap, fmt)
+            assert M == wm.shape[0]
+            assert np.array_equal(c, wc)
+            if M <= cap:
+                assert np.array_equal(m, wm)
