@@ -207,8 +207,10 @@ __device__ __forceinline__ uint32_t lean_careful(uint32_t s_in, uint64_t row, in
 
 // The matches of one queued stage per lane (has): the stage's 16 bytes (all
 // A/C/G/T or packed codes, every position inside the text and owned by its
-// row, at byte b0) walked again from s_in, emitting the output of every
-// flagged state through emit_warp. All 32 lanes call it together.
+// row, at byte b0) walked from s_in twice -- once to count the outputs, then,
+// after one slot reservation for the whole warp, to write them (one atomic
+// round trip per warp instead of one per symbol with an output). All 32
+// lanes call it together.
 template <int FMT, int LM>
 __device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_t b0, const ScanParams &p,
                                                 const SubsetDev &sd, const uint8_t *tab, uint32_t hot,
@@ -224,15 +226,45 @@ __device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_
     }
     const uint64_t pol = l2_evict_last();
     const uint64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
-    uint32_t sc = s_in;
+    uint32_t cnt = 0;
+    unsigned long long slot = 0;
 #pragma unroll 1
-    for (int e = 0; e < 4; ++e) {
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (uint32_t)o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) return;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(p.num, (unsigned long long)total);
+            slot = __shfl_sync(kFull, base, 0) + (incl - cnt);
+        }
+        uint32_t sc = s_in;
+#pragma unroll 1
+        for (int e = 0; e < 4; ++e) {
 #pragma unroll 4
-        for (int b = 0; b < PER; ++b) {
-            const uint32_t c = (FMT == FMT_U8) ? (w[e] >> (8 * b)) & 3u : (w[e] >> (2 * b)) & 3u;
-            const uint32_t nv = has ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
-            sc = nv & kStateMask;
-            emit_warp((nv & kFlag) != 0, sc, pos0 + (uint64_t)(e * PER + b), 0, sd, p, lane);
+            for (int b = 0; b < PER; ++b) {
+                const uint32_t c = (FMT == FMT_U8) ? (w[e] >> (8 * b)) & 3u : (w[e] >> (2 * b)) & 3u;
+                const uint32_t nv = has ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
+                sc = nv & kStateMask;
+                if (nv & kFlag) {
+                    const uint32_t o0 = __ldg(sd.out_off + sc), o1 = __ldg(sd.out_off + sc + 1);
+                    if (pass == 0) {
+                        cnt += o1 - o0;
+                    } else {
+                        const uint64_t pos = pos0 + (uint64_t)(e * PER + b);
+                        for (uint32_t t = o0; t < o1; ++t, ++slot) {
+                            const uint32_t id = __ldg(sd.out_ids + t);
+                            if (slot < p.cap) p.keys[slot] = (pos << p.key_shift) | id;
+                            if (p.counts) atomicAdd(p.counts + id, 1ull);
+                        }
+                    }
+                }
+            }
         }
     }
 }
