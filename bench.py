@@ -542,14 +542,21 @@ def bench_batch(A, torch, dev, args):
         res = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fl)
     batched_s = (time.perf_counter() - t0) / reps
     M = sum(m.shape[0] for m, _ in res)
-    # the default path for byte texts: one text per automaton
+    # the default path for byte texts: one text per automaton; the matches
+    # come back as one flat array with per-text offsets
     fs = A.AC_BATCH_NO_COUNTS
-    res_s = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs)
+    res_s = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs, flat=True)
     t0 = time.perf_counter()
     for _ in range(reps):
-        res_s = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs)
+        res_s = A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs, flat=True)
     segments_s = (time.perf_counter() - t0) / reps
-    M_s = sum(m.shape[0] for m, _ in res_s)
+    M_s = int(res_s[0].shape[0])
+    # the same with one (matches, counts) pair of array views per text
+    A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=fs)
+    segments_views_s = (time.perf_counter() - t0) / reps
     # the same with per-text dense count arrays copied to the host as well
     A.ac_scan_batch(autos, items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH)
     t0 = time.perf_counter()
@@ -580,13 +587,14 @@ def bench_batch(A, torch, dev, args):
             "per_call_GBps": total / per_call_s / 1e9, "per_call_ms": per_call_s * 1e3,
             "speedup": per_call_s / best_s,
             "one_text_per_automaton_ms": segments_s * 1e3, "one_launch_graph_ms": batched_s * 1e3,
+            "one_text_per_automaton_views_per_text_ms": segments_views_s * 1e3,
             "plan_and_autotune_ms": plan_s * 1e3,
             "one_launch_graph_with_counts_ms": counts_s * 1e3,
             "count_array_bytes": int(sum(autos[int(a)].num_patterns for a in w.set_of_text) * 8),
             "matches": M, "matches_one_text_per_automaton": M_s, "matches_per_call_path": M_calls,
-            "batched_path": ("ac_scan_batch(AC_DEVICE, AC_BATCH_NO_COUNTS): texts gathered one automaton at a time "
-                             "into one text behind separator bytes, one single-text scan + sort each, matches to "
-                             "the host per text") if segments_s <= batched_s else
+            "batched_path": ("ac_scan_batch(AC_DEVICE, AC_BATCH_NO_COUNTS, flat=True): texts gathered one "
+                             "automaton at a time into one text behind separator bytes, one single-text scan + sort "
+                             "each, matches to the host as one array with per-text offsets") if segments_s <= batched_s else
                             ("ac_scan_batch(AC_DEVICE, AC_BATCH_GRAPH|AC_BATCH_NO_COUNTS): arena copy + 1 "
                              "persistent scan + sort + records, matches to the host per text"),
             "per_call_path": "ac_scan_async per text (device results), one stream"}

@@ -240,12 +240,14 @@ _RESULT_DTYPE = np.dtype({"names": ["num_matches", "num_patterns"], "formats": [
                           "itemsize": C.sizeof(ac_result)})
 
 
-def _take_results(outs, n: int, want_counts: bool = True):
+def _take_results(outs, n: int, want_counts: bool = True, flat: bool = False):
     """Results outs[0..n) as ``(matches, counts)`` pairs: one copy out of the
     library into two flat arrays (ac_results_take, which releases the
-    results), each pair views into them; counts None unless want_counts."""
+    results), each pair views into them; counts None unless want_counts.
+    flat: the arrays themselves, ``(matches, moff, counts, coff)`` -- text i's
+    matches are ``matches[moff[i]:moff[i + 1]]`` (and its counts likewise)."""
     if n == 0:
-        return []
+        return (np.zeros((0, 2), np.uint32), np.zeros(1, np.uint64), None, None) if flat else []
     rec = np.frombuffer(outs, dtype=_RESULT_DTYPE, count=n)
     matches = np.empty((int(rec["num_matches"].sum()), 2), dtype=np.uint32)
     moff = np.empty(n + 1, dtype=np.uint64)
@@ -256,6 +258,8 @@ def _take_results(outs, n: int, want_counts: bool = True):
     _check(lib().ac_results_take(outs, n, matches.ctypes.data, moff.ctypes.data,
                                  counts.ctypes.data if want_counts else None,
                                  coff.ctypes.data if want_counts else None), "ac_results_take")
+    if flat:
+        return matches, moff, counts, coff
     mo = moff.tolist()
     ms = [matches[mo[i]:mo[i + 1]] for i in range(n)]
     if not want_counts:
@@ -431,10 +435,13 @@ _ITEM_DTYPE = np.dtype({"names": ["automaton", "fmt", "text", "n"], "formats": [
                         "itemsize": C.sizeof(ac_batch_item)})
 
 
-def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=None):
+def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=None, flat: bool = False):
     """``items``: list of ``(automaton_index, text, n, fmt)``; texts are host
     buffers (mem=AC_HOST) or CUDA tensors (mem=AC_DEVICE). Returns a list of
-    ``(matches, counts)`` (counts None with AC_BATCH_NO_COUNTS)."""
+    ``(matches, counts)`` (counts None with AC_BATCH_NO_COUNTS), or with
+    ``flat=True`` the flat arrays ``(matches, moff, counts, coff)``: item i's
+    matches are ``matches[moff[i]:moff[i + 1]]``, its counts
+    ``counts[coff[i]:coff[i + 1]]`` (no per-item array objects)."""
     hs = (C.c_void_p * max(1, len(automata)))(*[a.h for a in automata])
     # the item array filled column by column (one ctypes struct per item costs microseconds each)
     arr = np.zeros(max(1, len(items)), dtype=_ITEM_DTYPE)
@@ -460,7 +467,7 @@ def ac_scan_batch(automata, items, mem: int = AC_HOST, flags: int = 0, stream=No
     outs = (ac_result * max(1, len(items)))()
     _check(lib().ac_scan_batch(hs, len(automata), arr_p, len(items), mem, int(flags), _stream_ptr(stream), outs),
            "ac_scan_batch")
-    return _take_results(outs, len(items), not (flags & AC_BATCH_NO_COUNTS))
+    return _take_results(outs, len(items), not (flags & AC_BATCH_NO_COUNTS), flat)
 
 
 def ac_batch_release():

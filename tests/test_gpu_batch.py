@@ -154,3 +154,21 @@ def test_batch_errors():
     with pytest.raises(A.AcError) as e:
         A.ac_scan_batch([b], [(0, b"\x00", 4, A.AC_PACKED2)])
     assert e.value.code == A.AC_EINVAL
+
+
+def test_flat_results():
+    """flat=True: one matches array with per-text offsets, the same records
+    as the per-text pairs."""
+    rng = np.random.default_rng(44)
+    texts = [workloads.dna_text(rng, int(n)) for n in (0, 5, 3000, 70_000, 1)]
+    sets = make_sets(rng, [t for t in texts if t.size > 100], [80, 400], 4, 20)
+    autos = [A.ac_build(s, alphabet="ACGT") for s in sets]
+    items = [(i % 2, t, t.size, A.AC_U8) for i, t in enumerate(texts)]
+    pairs = A.ac_scan_batch(autos, items)
+    m, mo, c, co = A.ac_scan_batch(autos, items, flat=True)
+    assert mo.shape == (len(items) + 1,) and co.shape == (len(items) + 1,)
+    for i, (pm, pc) in enumerate(pairs):
+        assert np.array_equal(m[mo[i]:mo[i + 1]], pm)
+        assert np.array_equal(c[co[i]:co[i + 1]], pc)
+    m2, mo2, c2, co2 = A.ac_scan_batch(autos, items, flags=A.AC_BATCH_NO_COUNTS, flat=True)
+    assert np.array_equal(m2, m) and np.array_equal(mo2, mo) and c2 is None and co2 is None
