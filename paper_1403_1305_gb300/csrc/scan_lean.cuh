@@ -207,10 +207,12 @@ __device__ __forceinline__ uint32_t lean_careful(uint32_t s_in, uint64_t row, in
 
 // The matches of one queued stage per lane (has): the stage's 16 bytes (all
 // A/C/G/T or packed codes, every position inside the text and owned by its
-// row, at byte b0) walked from s_in twice -- once to count the outputs, then,
-// after one slot reservation for the whole warp, to write them (one atomic
-// round trip per warp instead of one per symbol with an output). All 32
-// lanes call it together.
+// row, at byte b0) walked again from s_in, counting the outputs and keeping
+// the last four flagged (state, step) pairs in registers; then one slot
+// reservation for the whole warp and the keys written from those pairs
+// (one dependent walk and one atomic round trip per warp). A lane with more
+// than four flagged steps makes the warp walk again to write. All 32 lanes
+// call it together.
 template <int FMT, int LM>
 __device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_t b0, const ScanParams &p,
                                                 const SubsetDev &sd, const uint8_t *tab, uint32_t hot,
@@ -226,23 +228,9 @@ __device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_
     }
     const uint64_t pol = l2_evict_last();
     const uint64_t pos0 = (FMT == FMT_U8) ? b0 : b0 * 4;
-    uint32_t cnt = 0;
-    unsigned long long slot = 0;
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= (uint32_t)o) incl += t;
-            }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            if (total == 0) return;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(p.num, (unsigned long long)total);
-            slot = __shfl_sync(kFull, base, 0) + (incl - cnt);
-        }
+    uint32_t cnt = 0, nrec = 0;
+    uint32_t rs0 = 0, rs1 = 0, rs2 = 0, rs3 = 0, rp0 = 0, rp1 = 0, rp2 = 0, rp3 = 0;  // newest first
+    {
         uint32_t sc = s_in;
 #pragma unroll 1
         for (int e = 0; e < 4; ++e) {
@@ -252,19 +240,51 @@ __device__ __forceinline__ void lean_emit_stage(bool has, uint32_t s_in, uint64_
                 const uint32_t nv = has ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
                 sc = nv & kStateMask;
                 if (nv & kFlag) {
-                    const uint32_t o0 = __ldg(sd.out_off + sc), o1 = __ldg(sd.out_off + sc + 1);
-                    if (pass == 0) {
-                        cnt += o1 - o0;
-                    } else {
-                        const uint64_t pos = pos0 + (uint64_t)(e * PER + b);
-                        for (uint32_t t = o0; t < o1; ++t, ++slot) {
-                            const uint32_t id = __ldg(sd.out_ids + t);
-                            if (slot < p.cap) p.keys[slot] = (pos << p.key_shift) | id;
-                            if (p.counts) atomicAdd(p.counts + id, 1ull);
-                        }
-                    }
+                    cnt += __ldg(sd.out_off + sc + 1) - __ldg(sd.out_off + sc);
+                    rs3 = rs2; rs2 = rs1; rs1 = rs0; rs0 = sc;
+                    rp3 = rp2; rp2 = rp1; rp1 = rp0; rp0 = (uint32_t)(e * PER + b);
+                    ++nrec;
                 }
             }
+        }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.num, (unsigned long long)total);
+    unsigned long long slot = __shfl_sync(kFull, base, 0) + (incl - cnt);
+    auto write = [&](uint32_t st, uint32_t step) {
+        const uint64_t pos = pos0 + step;
+        const uint32_t o0 = __ldg(sd.out_off + st), o1 = __ldg(sd.out_off + st + 1);
+        for (uint32_t t = o0; t < o1; ++t, ++slot) {
+            const uint32_t id = __ldg(sd.out_ids + t);
+            if (slot < p.cap) p.keys[slot] = (pos << p.key_shift) | id;
+            if (p.counts) atomicAdd(p.counts + id, 1ull);
+        }
+    };
+    if (!__any_sync(kFull, nrec > 4)) {
+        if (nrec > 0) write(rs0, rp0);
+        if (nrec > 1) write(rs1, rp1);
+        if (nrec > 2) write(rs2, rp2);
+        if (nrec > 3) write(rs3, rp3);
+        return;
+    }
+    // some lane has more flagged steps than it kept: walk again and write
+    uint32_t sc = s_in;
+#pragma unroll 1
+    for (int e = 0; e < 4; ++e) {
+#pragma unroll 4
+        for (int b = 0; b < PER; ++b) {
+            const uint32_t c = (FMT == FMT_U8) ? (w[e] >> (8 * b)) & 3u : (w[e] >> (2 * b)) & 3u;
+            const uint32_t nv = has ? lean_lookup<LM>(tab, hot, sd.table, sc, c, pol) : 0u;
+            sc = nv & kStateMask;
+            if (nv & kFlag) write(sc, (uint32_t)(e * PER + b));
         }
     }
 }
