@@ -502,6 +502,16 @@ typedef struct {
 AC_API int ac_probe_gather(int device, uint64_t table_bytes, int shared, uint32_t threads, uint32_t chains,
                            uint32_t steps, ac_gather_probe *out);
 
+/* The launch floor a chain of scan launches meets: enqueue `launches` empty
+ * kernels of `blocks` CTAs x `threads` threads, one after the other, on
+ * `stream` (a cudaStream_t; NULL is the legacy default stream) of the
+ * current device. Asynchronous; may be captured in a CUDA graph, where each
+ * launch is one kernel node depending on the one before it. Replaying a
+ * graph of empty nodes shaped like a scan call's device operations gives the
+ * time a call spends on launches alone. Errors: AC_EINVAL (launches,
+ * blocks or threads 0, threads over 1024), AC_ECUDA (a launch failed). */
+AC_API int ac_probe_launch(void *stream, uint32_t launches, uint32_t blocks, uint32_t threads);
+
 /* ------------------------------------------------------------ misc */
 AC_API const char *ac_strerror(int code);
 AC_API const char *ac_last_error(void);

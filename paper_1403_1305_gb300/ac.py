@@ -35,7 +35,7 @@ EXPORTED = (
     "ac_build", "ac_free", "ac_save", "ac_load", "ac_stats", "ac_subset", "ac_set_scan_config", "ac_get_scan_config", "ac_tune",
     "ac_scan", "ac_scan_async", "ac_scan_keys_async", "ac_key_shift", "ac_sort_keys_async", "ac_scan_noalloc", "ac_scan_batch", "ac_batch_release", "ac_result_free", "ac_results_take", "ac_serve_create", "ac_serve_submit", "ac_serve_submit_at",
     "ac_serve_poll", "ac_serve_wait", "ac_serve_stats", "ac_serve_destroy", "ac_strerror", "ac_last_error",
-    "ac_version", "ac_probe_gather",
+    "ac_version", "ac_probe_gather", "ac_probe_launch",
 )
 
 
@@ -146,6 +146,7 @@ def _declare(lib):
         "ac_last_error": (C.c_char_p, []),
         "ac_version": (C.c_int, []),
         "ac_probe_gather": (C.c_int, [C.c_int, u64, C.c_int, u32, u32, u32, C.POINTER(ac_gather_probe)]),
+        "ac_probe_launch": (C.c_int, [C.c_void_p, u32, u32, u32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -567,3 +568,9 @@ def ac_probe_gather(device: int, table_bytes: int, shared: bool = False, threads
     _check(lib().ac_probe_gather(int(device), int(table_bytes), int(bool(shared)), int(threads), int(chains),
                                  int(steps), C.byref(out)), "ac_probe_gather")
     return {f: getattr(out, f) for f, _ in ac_gather_probe._fields_}
+
+
+def ac_probe_launch(stream=None, launches: int = 1, blocks: int = 1, threads: int = 32) -> None:
+    """Enqueue ``launches`` empty kernels on ``stream`` (capturable in a CUDA
+    graph): the launch floor of a chain of device operations."""
+    _check(lib().ac_probe_launch(_stream_ptr(stream), int(launches), int(blocks), int(threads)), "ac_probe_launch")

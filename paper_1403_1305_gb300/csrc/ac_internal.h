@@ -176,6 +176,10 @@ struct ScanOut {
     // null: stages with matches are walked again in place
     EmitEntry *q = nullptr;
     uint64_t q_cap = 0;
+    // the scan kernel may start while the launch before it in the stream (the
+    // zeroing of num and counts) still runs; it waits for that launch's
+    // writes before its own first write to num, counts or keys
+    bool after_zero = false;
 };
 
 // Stage geometry shared by host planning and the kernels.
@@ -213,6 +217,7 @@ struct ScanPlan {
     uint32_t stride = 1;
     uint32_t smem_rows = 0;
     uint32_t table_words = 0;
+    uint32_t out_words = 0;  // short-text kernel: output offsets and ids staged in shared memory (0: read from global)
     size_t smem = 0;
 };
 int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out);
@@ -256,10 +261,19 @@ int launch_keys_to_matches(const unsigned long long *keys, const unsigned long l
 int key_shift_for(const ac_automaton *a);
 int launch_pad_keys(unsigned long long *keys, const unsigned long long *num, uint64_t cap, cudaStream_t stream);
 int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t stream);
+// One-time process state of the scan launches (the tensor-map encoder, the
+// rank sort's shared-memory attribute), set up before a first call that may
+// run under stream capture.
+void prime_scan_state();
+
 // single-launch sort + record conversion of the first min(*num, cap) keys, cap at most kSmallSortMax
 constexpr uint64_t kSmallSortMax = 8192;
+// overlap: the sort may start while the launch before it in the stream (one
+// of this library's scan or zeroing kernels) still runs; it waits for that
+// launch's writes before reading anything
 int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, uint32_t shift,
-                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream);
+                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream,
+                      bool overlap = false);
 int sort_keys(unsigned long long *keys, unsigned long long *keys_alt, uint64_t count, int begin_bit, int end_bit,
               void *temp, size_t *temp_bytes, cudaStream_t stream, unsigned long long **sorted);
 // first key bit a sort of a's keys must look at (stable sorts)

@@ -253,6 +253,10 @@ static int upload(ac_automaton *a) {
     CK(cudaMalloc(&a->d_desc, sizeof(SubsetDev) * a->K), "ac_build: descriptors");
     CK(cudaMemcpy(a->d_desc, a->h_desc.data(), sizeof(SubsetDev) * a->K, cudaMemcpyHostToDevice),
        "ac_build: descriptors");
+    // the scratch pool and the launches' one-time state exist before the first
+    // scan, which may be under stream capture (where creating them is refused)
+    (void)pool_for(a->device);
+    prime_scan_state();
     a->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return AC_OK;
 }
@@ -1021,6 +1025,7 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
         ScanText tx{t, n, fmt, readable};
         ScanOut o{(unsigned long long *)d_keys, cap, (unsigned long long *)d_num, (unsigned long long *)d_counts,
                   err};
+        o.after_zero = true;  // the zeroing launch is the one just before
         if (q) {
             o.q = q;
             o.q_cap = q_cap;
@@ -1049,12 +1054,16 @@ int ac_scan_keys_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n,
 }
 
 // The sort of the keys into records; err (or null): a scan's error word,
-// reported as *d_num_out = UINT64_MAX.
+// reported as *d_num_out = UINT64_MAX. overlap: the launch just before is
+// this library's scan or zeroing, and the one-launch sort may start while it
+// finishes (it waits for its writes).
 static int sort_to_matches(const ac_automaton *a, uint64_t n, uint64_t *d_keys, const uint64_t *d_num, uint64_t cap,
-                           cudaStream_t s, ac_match *d_matches, uint64_t *d_num_out, const uint32_t *err) {
+                           cudaStream_t s, ac_match *d_matches, uint64_t *d_num_out, const uint32_t *err,
+                           bool overlap = false) {
     if (cap <= kSmallSortMax)
         return launch_small_sort((const unsigned long long *)d_keys, (const unsigned long long *)d_num, cap,
-                                 (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, err, s);
+                                 (uint32_t)key_shift_for(a), d_matches, (unsigned long long *)d_num_out, err, s,
+                                 overlap);
     Scratch sc(s);
     const uint64_t kcap = cap ? cap : 1;
     unsigned long long *alt = (unsigned long long *)sc.get(kcap * 8);
@@ -1106,7 +1115,7 @@ int ac_scan_async(const ac_automaton *a, const uint8_t *d_text, uint64_t n, int 
     const uint32_t *err = nullptr;
     rc = scan_keys(a, d_text, n, fmt, s, sc, keys, cap, d_num_matches, d_counts, &err);
     if (rc) return rc;
-    return sort_to_matches(a, n, keys, d_num_matches, cap, s, d_matches, d_num_matches, err);
+    return sort_to_matches(a, n, keys, d_num_matches, cap, s, d_matches, d_num_matches, err, true);
 }
 
 }  // extern "C"

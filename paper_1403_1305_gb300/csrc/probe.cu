@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(1024, 1)
     if (acc == 0x9e3779b9u) sink[0] = acc;
 }
 
+__global__ void probe_empty_kernel() {}
+
 using ProbeFn = void (*)(const uint32_t *, uint32_t, uint32_t, uint32_t *);
 
 ProbeFn pick(bool shared, uint32_t chains) {
@@ -153,4 +155,13 @@ extern "C" int ac_probe_gather(int device, uint64_t table_bytes, int shared, uin
     if (buf) cudaFree(buf);
     cudaSetDevice(prev);
     return rc;
+}
+
+extern "C" int ac_probe_launch(void *stream, uint32_t launches, uint32_t blocks, uint32_t threads) {
+    if (!launches || !blocks || !threads || threads > 1024)
+        return set_error(AC_EINVAL, "ac_probe_launch: launches, blocks and threads must be positive, threads <= 1024");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t i = 0; i < launches; ++i) probe_empty_kernel<<<blocks, threads, 0, s>>>();
+    if (cudaGetLastError() != cudaSuccess) return set_error(AC_ECUDA, "ac_probe_launch: launch failed");
+    return AC_OK;
 }

@@ -13,6 +13,31 @@ using namespace kern;
 
 namespace {
 
+// A launch that, with `overlap`, may start before the launch ahead of it in
+// the stream has finished (programmatic stream serialization; in a captured
+// graph, a programmatic edge): the kernel calls pdl_wait() before it touches
+// that launch's results. Without `overlap`, an ordinary launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_overlapped(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              bool overlap, Args... args) {
+    if (!overlap) {
+        fn<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, args...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ small kernels
 __global__ void fill_u64_kernel(unsigned long long *p, uint64_t count, unsigned long long value) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
@@ -21,6 +46,7 @@ __global__ void fill_u64_kernel(unsigned long long *p, uint64_t count, unsigned 
 
 __global__ void zero3_kernel(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1,
                              unsigned long long *p2, uint64_t n2) {
+    kern::pdl_release();  // a scan or sort behind it may start; it waits for these writes
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n0 + n1 + n2; i += stride) {
         if (i < n0) p0[i] = 0;
@@ -408,6 +434,10 @@ static int plan_short(const ac_automaton *a, const ac_scan_config &cfg, int fmt,
         pl.mode = kern::SHORT_FULL;
         pl.smem_rows = d.states;
         pl.table_words = d.states * 4;
+        // the output lists beside the table when they fit too: a flagged
+        // state's outputs are then read without a global round trip
+        const uint64_t ow = (uint64_t)d.states + 1 + a->subs[0].out_ids.size();
+        if ((uint64_t)d.states * 16 + ow * 4 <= room) pl.out_words = (uint32_t)ow;
     } else {
         if (a->placement == AC_PLACE_SMEM)
             return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory", d.states);
@@ -416,7 +446,7 @@ static int plan_short(const ac_automaton *a, const ac_scan_config &cfg, int fmt,
         pl.smem_rows = (uint32_t)std::min<uint64_t>(d.rows_e16, room / 8);
         pl.table_words = (pl.smem_rows * 2 + 3) & ~3u;
     }
-    pl.smem = (size_t)pl.table_words * 4 + 256;
+    pl.smem = (size_t)pl.table_words * 4 + 256 + (size_t)pl.out_words * 4;
     *out = pl;
     return AC_OK;
 }
@@ -706,6 +736,8 @@ static int launch_short(const ac_automaton *a, const ScanText &t, const ScanOut 
     p.K = 1;
     p.sigma = a->sigma;
     p.subs = a->d_desc;
+    p.sub0 = a->h_desc[0];
+    p.out_words = plan.out_words;
     p.keys = o.keys;
     p.cap = o.cap;
     p.num = o.num;
@@ -725,8 +757,7 @@ static int launch_short(const ac_automaton *a, const ScanText &t, const ScanOut 
                                                                             : kern::short_u8_e16(words, a->dna_acgt));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan: %s", cudaGetErrorString(e));
-    fn<<<(unsigned)grid, threads, plan.smem, stream>>>(p);
-    e = cudaGetLastError();
+    e = launch_overlapped(fn, dim3((unsigned)grid), dim3(threads), plan.smem, stream, o.after_zero, p);
     if (e != cudaSuccess) return set_error(AC_ECUDA, "scan launch: %s", cudaGetErrorString(e));
     return AC_OK;
 }
@@ -882,6 +913,7 @@ __global__ void __launch_bounds__(kRankThreads)
                      uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out, const uint32_t *err) {
     extern __shared__ __align__(16) unsigned long long sk[];  // pairs(cap) * 2 keys
     __shared__ uint32_t part[kRankGroups][2][kRankPer];      // per group: each warp's counts
+    kern::pdl_wait();  // the keys, the counter and the error word of the launch before
     const unsigned long long M = *num;  // num_out may be num: read before anything is written
     const bool failed = err && *err;
     if (blockIdx.x == 0 && threadIdx.x == 0 && num_out) *num_out = failed ? ~0ull : M;
@@ -943,21 +975,33 @@ __global__ void __launch_bounds__(kRankThreads)
 }
 }  // namespace
 
-int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, uint32_t shift,
-                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream) {
-    if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
-                                              (unsigned long long)kSmallSortMax);
-    const int smem = (int)(((cap + 1) / 2 + 1) * 16);
+// The rank sort's shared-memory attribute, set once per process.
+static cudaError_t small_sort_attr() {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(rank_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)((kSmallSortMax / 2 + 1) * 16));
     });
+    return attr;
+}
+
+void prime_scan_state() {
+    (void)encoder();
+    (void)small_sort_attr();
+}
+
+int launch_small_sort(const unsigned long long *keys, const unsigned long long *num, uint64_t cap, uint32_t shift,
+                      ac_match *out, unsigned long long *num_out, const uint32_t *err, cudaStream_t stream,
+                      bool overlap) {
+    if (cap > kSmallSortMax) return set_error(AC_EINVAL, "small sort: capacity above %llu",
+                                              (unsigned long long)kSmallSortMax);
+    const int smem = (int)(((cap + 1) / 2 + 1) * 16);
+    const cudaError_t attr = small_sort_attr();
     if (attr != cudaSuccess) return set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(attr));
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, (cap + kRankKeys - 1) / kRankKeys);
-    rank_sort_kernel<<<grid, kRankThreads, smem, stream>>>(keys, num, cap, shift, out, num_out, err);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_overlapped(rank_sort_kernel, dim3(grid), dim3(kRankThreads), (size_t)smem, stream, overlap,
+                                      keys, num, cap, shift, out, num_out, err);
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "small sort: %s", cudaGetErrorString(e));
 }
 

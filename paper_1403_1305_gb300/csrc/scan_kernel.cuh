@@ -94,9 +94,22 @@ struct ScanParams {
     const BatchTileDev *tiles;  // one per tile: machine and first row
     uint32_t num_items;
     uint8_t sym_of_byte[256];
+    // short-text kernel: the machine's descriptor (a copy of subs[0]) and the
+    // words of its output lists (offsets, then ids) staged in shared memory
+    // (0: read from global memory)
+    SubsetDev sub0;
+    uint32_t out_words;
 };
 
 // ------------------------------------------------------------------ PTX helpers
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before the launch ahead of it in the stream has
+// finished; pdl_wait() returns once that launch has completed and its writes
+// are visible (at once for a kernel launched without the attribute), and
+// pdl_release() lets the launch behind this one start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -109,6 +109,94 @@ __device__ __forceinline__ uint32_t short_fast_word(const uint4 &v, uint32_t &s,
     return acc;
 }
 
+// The outputs of one row word per lane (has: the word is wholly inside the
+// text and, for bytes, wholly A/C/G/T, and its walk met a flagged state):
+// the word walked again from s_in, counting the outputs and keeping the last
+// four flagged steps in registers (state << 6 | step; machines of fewer than
+// 2^26 states), then one slot reservation for the whole warp and the keys
+// written from those records; a lane with more than four flagged steps (or a
+// larger machine) makes the warp walk the word once more to write.
+// pos0: position of the word's first symbol. ooff / oids: the output offsets
+// and ids (shared or global memory). All 32 lanes call it together.
+template <int FMT, int SM>
+__device__ __forceinline__ void short_emit_word(bool has, const uint4 &v, uint32_t s_in, uint64_t pos0,
+                                                uint32_t sbase, uint32_t hot, const uint32_t *gtab,
+                                                const uint32_t *ooff, const uint32_t *oids, const ScanParams &p,
+                                                uint32_t lane) {
+    constexpr uint32_t SH = (SM == SHORT_FULL) ? 2 : 1;  // code -> byte offset in the row
+    constexpr int PER = (FMT == FMT_U8) ? 4 : 16;        // symbols per 32-bit word
+    auto step = [&](uint32_t s, uint32_t cw, int b) -> uint32_t {
+        uint32_t off;
+        if (FMT == FMT_U8) off = __byte_perm(cw, 0, 0x4440 + b);
+        else off = ((2 * b >= (int)SH) ? (cw >> (2 * b - SH)) : (cw << (SH - 2 * b))) & (3u << SH);
+        if (SM == SHORT_FULL) return lds_u32(sbase + (s << 4) + off);
+        const uint32_t gi = (s << 3) + off;
+        return short_e16(s, sbase + gi, gi, hot, gtab);
+    };
+    uint32_t cnt = 0, nrec = 0;
+    uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;  // newest first
+    if (has) {
+        uint32_t s = s_in;
+#pragma unroll 1
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t x = word_of(v, e);
+            const uint32_t cw = (FMT == FMT_U8) ? (acgt_codes4(x) << SH) : x;
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const uint32_t nv = step(s, cw, b);
+                s = nv & kStateMask;
+                if (nv & kFlag) {
+                    cnt += ooff[s + 1] - ooff[s];
+                    r3 = r2; r2 = r1; r1 = r0; r0 = (s << 6) | (uint32_t)(e * PER + b);
+                    ++nrec;
+                }
+            }
+        }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.num, (unsigned long long)total);
+    unsigned long long slot = __shfl_sync(kFull, base, 0) + (incl - cnt);
+    auto write = [&](uint32_t st, uint32_t k) {
+        const uint64_t pos = pos0 + k;
+        const uint32_t o0 = ooff[st], o1 = ooff[st + 1];
+        for (uint32_t t = o0; t < o1; ++t, ++slot) {
+            const uint32_t id = oids[t];
+            if (slot < p.cap) p.keys[slot] = (pos << p.key_shift) | id;
+            if (p.counts) atomicAdd(p.counts + id, 1ull);
+        }
+    };
+    if (!__any_sync(kFull, nrec > 4) && p.sub0.states < (1u << 26)) {
+        if (nrec > 0) write(r0 >> 6, r0 & 63u);
+        if (nrec > 1) write(r1 >> 6, r1 & 63u);
+        if (nrec > 2) write(r2 >> 6, r2 & 63u);
+        if (nrec > 3) write(r3 >> 6, r3 & 63u);
+        return;
+    }
+    // some lane has more flagged steps than it kept: walk again and write
+    if (has) {
+        uint32_t s = s_in;
+#pragma unroll 1
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t x = word_of(v, e);
+            const uint32_t cw = (FMT == FMT_U8) ? (acgt_codes4(x) << SH) : x;
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const uint32_t nv = step(s, cw, b);
+                s = nv & kStateMask;
+                if (nv & kFlag) write(s, (uint32_t)(e * PER + b));
+            }
+        }
+    }
+}
+
 // all 16 bytes of the word are A, C, G or T
 __device__ __forceinline__ bool word_is_acgt(const uint4 &v) {
     return (acgt_mismatch4(v.x, acgt_codes4(v.x)) | acgt_mismatch4(v.y, acgt_codes4(v.y)) |
@@ -120,7 +208,8 @@ __device__ __forceinline__ bool word_is_acgt(const uint4 &v) {
 template <int FMT, int SM, int MAXW, bool ACGT>
 __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ ScanParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
-    const SubsetDev &sd = *p.subs;
+    pdl_release();  // the sort behind this launch may start; it waits for these results
+    const SubsetDev &sd = p.sub0;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warm_bytes = (FMT == FMT_U8) ? sd.warm : (sd.warm + 3) / 4;
     const uint32_t nw_warm = (warm_bytes + 15) / 16;
@@ -152,6 +241,7 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
     const uint32_t tbytes = (SM == SHORT_FULL) ? sd.states * 16u : p.smem_rows * 8u;
     uint8_t *tab = smem;
     uint8_t *smap = smem + ((tbytes + 15) & ~15u);
+    uint32_t *outs = reinterpret_cast<uint32_t *>(smap + 256);  // output offsets, then ids (p.out_words)
     {
         const uint4 *src = (SM == SHORT_FULL) ? reinterpret_cast<const uint4 *>(sd.table)
                                               : reinterpret_cast<const uint4 *>(sd.table_e16);
@@ -164,10 +254,20 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
         if ((tbytes & 15) && threadIdx.x == 0)  // an odd row count of the 16-bit prefix: its last 8 bytes
             *reinterpret_cast<uint2 *>(tab + (tbytes & ~15u)) =
                 __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(src) + (tbytes & ~15u)));
+        const uint32_t odst = smem_addr(outs);
+        for (uint32_t i = threadIdx.x; i < p.out_words; i += blockDim.x) {
+            const uint32_t *osrc = i <= sd.states ? sd.out_off + i : sd.out_ids + (i - sd.states - 1);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(odst + 4 * i), "l"(osrc) : "memory");
+        }
         for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
+    const uint32_t *ooff = p.out_words ? outs : sd.out_off;
+    const uint32_t *oids = p.out_words ? outs + sd.states + 1 : sd.out_ids;
+    // the counter, counts and keys are written below: the launch before this
+    // one (their zeroing) has finished by now
+    pdl_wait();
 
     // The walk, one word at a time (the window shifts down one word per
     // step): warm-up words from the root (positions before the text start
@@ -206,15 +306,25 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
                 }
             }
         }
-        if (k >= nw_warm && __any_sync(kFull, (acc & kFlag) != 0)) {
-            s = s_in;
+        if (k >= nw_warm) {
+            // flagged words on the fast path: one walk and one reservation
+            // per warp; words at a text edge or holding other bytes (rare):
+            // symbol by symbol with every check
+            const bool flagged = (acc & kFlag) != 0;
+            if (__any_sync(kFull, fast && flagged))
+                short_emit_word<FMT, SM>(fast && flagged, cur, s_in, (uint64_t)(pos0 < 0 ? 0 : pos0), smem_addr(tab),
+                                         hot, sd.table, ooff, oids, p, lane);
+            const bool hard = !fast && flagged;
+            if (__any_sync(kFull, hard)) {
+                uint32_t sc = s_in;
 #pragma unroll 1
-            for (uint32_t i = 0; i < SYM; ++i) {
-                const int64_t pos = pos0 + i;
-                const uint32_t nv = short_step<SM>(s, word_symbol<FMT>(cur, i, smap), tab, hot, sd.table);
-                const bool live = active && pos >= 0 && pos < nsym;
-                s = live ? (nv & kStateMask) : 0u;
-                emit_warp(live && (nv & kFlag), s, (uint64_t)(pos < 0 ? 0 : pos), 0, sd, p, lane);
+                for (uint32_t i = 0; i < SYM; ++i) {
+                    const int64_t pos = pos0 + i;
+                    const uint32_t nv = short_step<SM>(sc, word_symbol<FMT>(cur, i, smap), tab, hot, sd.table);
+                    const bool live = active && pos >= 0 && pos < nsym;
+                    sc = live ? (nv & kStateMask) : 0u;
+                    emit_warp(hard && live && (nv & kFlag), sc, (uint64_t)(pos < 0 ? 0 : pos), 0, sd, p, lane);
+                }
             }
         }
     }
