@@ -217,7 +217,6 @@ struct ScanPlan {
     uint32_t stride = 1;
     uint32_t smem_rows = 0;
     uint32_t table_words = 0;
-    uint32_t out_words = 0;  // short-text kernel: output offsets and ids staged in shared memory (0: read from global)
     size_t smem = 0;
 };
 int plan_scan(const ac_automaton *a, const ac_scan_config &cfg, int fmt, ScanPlan *out);

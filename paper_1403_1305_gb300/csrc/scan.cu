@@ -434,10 +434,6 @@ static int plan_short(const ac_automaton *a, const ac_scan_config &cfg, int fmt,
         pl.mode = kern::SHORT_FULL;
         pl.smem_rows = d.states;
         pl.table_words = d.states * 4;
-        // the output lists beside the table when they fit too: a flagged
-        // state's outputs are then read without a global round trip
-        const uint64_t ow = (uint64_t)d.states + 1 + a->subs[0].out_ids.size();
-        if ((uint64_t)d.states * 16 + ow * 4 <= room) pl.out_words = (uint32_t)ow;
     } else {
         if (a->placement == AC_PLACE_SMEM)
             return set_error(AC_ERANGE, "scan: table of %u states does not fit in shared memory", d.states);
@@ -446,7 +442,7 @@ static int plan_short(const ac_automaton *a, const ac_scan_config &cfg, int fmt,
         pl.smem_rows = (uint32_t)std::min<uint64_t>(d.rows_e16, room / 8);
         pl.table_words = (pl.smem_rows * 2 + 3) & ~3u;
     }
-    pl.smem = (size_t)pl.table_words * 4 + 256 + (size_t)pl.out_words * 4;
+    pl.smem = (size_t)pl.table_words * 4 + 256;
     *out = pl;
     return AC_OK;
 }
@@ -737,7 +733,6 @@ static int launch_short(const ac_automaton *a, const ScanText &t, const ScanOut 
     p.sigma = a->sigma;
     p.subs = a->d_desc;
     p.sub0 = a->h_desc[0];
-    p.out_words = plan.out_words;
     p.keys = o.keys;
     p.cap = o.cap;
     p.num = o.num;
@@ -898,7 +893,8 @@ int launch_mark_error(unsigned long long *num, const uint32_t *err, cudaStream_t
 // (position, pattern) pair each), so a key's place in the sorted order is the
 // number of keys below it and each key is written straight there -- one
 // launch, no digit passes. A CTA copies all the keys into shared memory
-// (asynchronous 16-byte copies, one round trip) and ranks 32 of them: a thread
+// (asynchronous 16-byte copies; the first kRankEarly are requested before the
+// key count has arrived, so a short list costs one round trip) and ranks 32 of them: a thread
 // holds 4 keys and counts the keys below them in one of 64 interleaved slices
 // of the key array (read 16 bytes at once, each read serving 8 comparisons);
 // the slices' counts are summed with shuffles and then across the two warps
@@ -907,6 +903,7 @@ namespace {
 constexpr uint32_t kRankKeys = 32, kRankPer = 4, kRankPhases = 64;
 constexpr uint32_t kRankGroups = kRankKeys / kRankPer;        // 8 groups of 4 keys
 constexpr uint32_t kRankThreads = kRankGroups * kRankPhases;  // 512: a group is two warps
+constexpr uint32_t kRankEarly = 512;                           // keys copied before the count is known
 
 __global__ void __launch_bounds__(kRankThreads)
     rank_sort_kernel(const unsigned long long *__restrict__ keys, const unsigned long long *num, uint64_t cap,
@@ -914,35 +911,49 @@ __global__ void __launch_bounds__(kRankThreads)
     extern __shared__ __align__(16) unsigned long long sk[];  // pairs(cap) * 2 keys
     __shared__ uint32_t part[kRankGroups][2][kRankPer];      // per group: each warp's counts
     kern::pdl_wait();  // the keys, the counter and the error word of the launch before
+    const uint32_t base = smem_addr(sk);
+    const bool aligned = ((uintptr_t)keys & 15) == 0;
+    // the first keys' copies go out with the count's read (copies past the
+    // count read unused entries of the buffer, never past its capacity)
+    const uint32_t early = (uint32_t)(cap < kRankEarly ? cap : kRankEarly) / 2;  // pairs
+    if (aligned && blockIdx.x * kRankKeys < cap)
+        for (uint32_t t = threadIdx.x; t < early; t += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16 * t), "l"(keys + 2 * t)
+                         : "memory");
     const unsigned long long M = *num;  // num_out may be num: read before anything is written
     const bool failed = err && *err;
     if (blockIdx.x == 0 && threadIdx.x == 0 && num_out) *num_out = failed ? ~0ull : M;
     const uint32_t m = (uint32_t)(M < cap ? M : cap);
     const uint32_t kb = blockIdx.x * kRankKeys;
-    if (failed || kb >= m) return;  // uniform across the CTA
+    if (failed || kb >= m) {  // uniform across the CTA
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
+        return;
+    }
     const uint32_t pairs = (m + 1) / 2;
-    const uint32_t base = smem_addr(sk);
-    // an odd count's last pair is the last key and the all-ones pad (never below a key)
-    if (((uintptr_t)keys & 15) == 0) {
-        for (uint32_t t = threadIdx.x; t < m / 2; t += blockDim.x)
+    if (aligned) {
+        for (uint32_t t = early + threadIdx.x; t < m / 2; t += blockDim.x)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16 * t), "l"(keys + 2 * t)
                          : "memory");
     } else {  // keys only 8-byte aligned
         for (uint32_t t = threadIdx.x; t < m / 2 * 2; t += blockDim.x) sk[t] = keys[t];
     }
+    const unsigned long long last = (m & 1) && threadIdx.x == 0 ? keys[m - 1] : 0ull;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // an odd count's last pair is the last key and the all-ones pad (never
+    // below a key), written once every copy has landed
     if ((m & 1) && threadIdx.x == 0) {
-        sk[m - 1] = keys[m - 1];
+        sk[m - 1] = last;
         sk[m] = ~0ull;
     }
+    __syncthreads();
     const uint32_t ph = threadIdx.x % kRankPhases, grp = threadIdx.x / kRankPhases;
     unsigned long long ki[kRankPer];
 #pragma unroll
     for (uint32_t r = 0; r < kRankPer; ++r) {
         const uint32_t i = kb + grp * kRankPer + r;
-        ki[r] = i < m ? keys[i] : ~0ull;
+        ki[r] = i < m ? sk[i] : ~0ull;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
     const uint4 *sk4 = reinterpret_cast<const uint4 *>(sk);
     uint32_t below[kRankPer] = {0, 0, 0, 0};
 #pragma unroll 2

@@ -94,11 +94,8 @@ struct ScanParams {
     const BatchTileDev *tiles;  // one per tile: machine and first row
     uint32_t num_items;
     uint8_t sym_of_byte[256];
-    // short-text kernel: the machine's descriptor (a copy of subs[0]) and the
-    // words of its output lists (offsets, then ids) staged in shared memory
-    // (0: read from global memory)
+    // short-text kernel: the machine's descriptor (a copy of subs[0])
     SubsetDev sub0;
-    uint32_t out_words;
 };
 
 // ------------------------------------------------------------------ PTX helpers

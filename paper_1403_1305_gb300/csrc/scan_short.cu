@@ -117,7 +117,7 @@ __device__ __forceinline__ uint32_t short_fast_word(const uint4 &v, uint32_t &s,
 // written from those records; a lane with more than four flagged steps (or a
 // larger machine) makes the warp walk the word once more to write.
 // pos0: position of the word's first symbol. ooff / oids: the output offsets
-// and ids (shared or global memory). All 32 lanes call it together.
+// and ids. All 32 lanes call it together.
 template <int FMT, int SM>
 __device__ __forceinline__ void short_emit_word(bool has, const uint4 &v, uint32_t s_in, uint64_t pos0,
                                                 uint32_t sbase, uint32_t hot, const uint32_t *gtab,
@@ -241,7 +241,6 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
     const uint32_t tbytes = (SM == SHORT_FULL) ? sd.states * 16u : p.smem_rows * 8u;
     uint8_t *tab = smem;
     uint8_t *smap = smem + ((tbytes + 15) & ~15u);
-    uint32_t *outs = reinterpret_cast<uint32_t *>(smap + 256);  // output offsets, then ids (p.out_words)
     {
         const uint4 *src = (SM == SHORT_FULL) ? reinterpret_cast<const uint4 *>(sd.table)
                                               : reinterpret_cast<const uint4 *>(sd.table_e16);
@@ -254,17 +253,12 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
         if ((tbytes & 15) && threadIdx.x == 0)  // an odd row count of the 16-bit prefix: its last 8 bytes
             *reinterpret_cast<uint2 *>(tab + (tbytes & ~15u)) =
                 __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(src) + (tbytes & ~15u)));
-        const uint32_t odst = smem_addr(outs);
-        for (uint32_t i = threadIdx.x; i < p.out_words; i += blockDim.x) {
-            const uint32_t *osrc = i <= sd.states ? sd.out_off + i : sd.out_ids + (i - sd.states - 1);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(odst + 4 * i), "l"(osrc) : "memory");
-        }
         for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
-    const uint32_t *ooff = p.out_words ? outs : sd.out_off;
-    const uint32_t *oids = p.out_words ? outs + sd.states + 1 : sd.out_ids;
+    const uint32_t *ooff = sd.out_off;
+    const uint32_t *oids = sd.out_ids;
     // the counter, counts and keys are written below: the launch before this
     // one (their zeroing) has finished by now
     pdl_wait();
