@@ -398,6 +398,26 @@ def bench_configs(A, torch, dev, hbm_peak):
         graph_ok = False
         graph_ms = None
         out["config1_graph_error"] = str(ex)[:200]
+    # the launch floor of that graph: per call, three empty kernels (the
+    # call's device operations: zeroing, scan, sort) in the same chain
+    floor_ms = None
+    try:
+        gf = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gf, stream=stream):
+            cs = torch.cuda.current_stream()
+            for _ in range(100):
+                A.ac_probe_launch(cs, 3, 128, 512)
+        gf.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            gf.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        floor_ms = e0.elapsed_time(e1) / 1000
+    except Exception as ex:
+        out["config1_floor_error"] = str(ex)[:200]
     # steady state as one batch of 1000 copies of the text
     items = [(0, d, n, A.AC_U8)] * 1000
     A.ac_scan_batch([a], items, mem=A.AC_DEVICE, flags=A.AC_BATCH_GRAPH | A.AC_BATCH_NO_COUNTS)
@@ -410,6 +430,9 @@ def bench_configs(A, torch, dev, hbm_peak):
     roof_ms = n / (hbm_peak * 1e9) * 1e3
     out["config1"] = {"workload": w.name, "matches": M, "single_call_device_ms": ms, "single_call_wall_ms": wall_ms,
                       "graph_replayed_ms_per_scan": graph_ms, "batch1000_ms_per_scan": batch_ms,
+                      "graph_launch_floor_ms_per_scan": floor_ms,
+                      "graph_launch_floor_note": "100 x three empty kernels (128 x 512 threads) in one graph, "
+                                                 "the same chain of launches as a call, replayed",
                       "GBps_single": n / ms / 1e6, "GBps_graph": (n / graph_ms / 1e6) if graph_ok else None,
                       "GBps_batch1000": n / batch_ms / 1e6, "roofline_ms": roof_ms,
                       "frac_graph": (roof_ms / graph_ms) if graph_ok else None, "frac_batch1000": roof_ms / batch_ms}
@@ -768,7 +791,8 @@ def summary(line):
         c1 = c["config1"]
         out["config1_us"] = {"one_call": _r(c1["single_call_device_ms"] * 1e3),
                              "graph": _r((c1["graph_replayed_ms_per_scan"] or 0) * 1e3),
-                             "batch1000": _r(c1["batch1000_ms_per_scan"] * 1e3)}
+                             "batch1000": _r(c1["batch1000_ms_per_scan"] * 1e3),
+                             "graph_launch_floor": _r((c1.get("graph_launch_floor_ms_per_scan") or 0) * 1e3)}
     if "config3" in c:
         out["config3"] = {"ms": _r(c["config3"]["median_ms"]), "frac_l2": _r(c["config3"]["frac_of_l2_lookup_ceiling"])}
     if g("pfac"):

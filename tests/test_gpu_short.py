@@ -9,9 +9,10 @@ rest read through L2, down to a prefix of a few rows), every row length
 and several CTA sizes, text lengths around the 16-byte word and the row
 (0, 1, 15, 16, 17, ...), ragged packed tails, bytes outside the alphabet,
 a 4-letter alphabet other than ACGT, patterns long enough to need the
-nine-word window, matches at the first and last positions, host and device
-texts, a host text long enough for the pipelined copy (row ranges), the
-tuner's choice, and refusals where the kernel does not apply.
+nine-word window, rows that begin inside long occurrences, matches at the
+first and last positions, host and device texts, a host text long enough
+for the pipelined copy (row ranges), the tuner's choice, and refusals where
+the kernel does not apply.
 """
 import os
 
@@ -134,6 +135,30 @@ def test_long_patterns_need_the_wide_window(max_len):
             assert e.value.code == A.AC_EINVAL
             continue
         all_paths(a, text, want)
+
+
+@pytest.mark.parametrize("L", [17, 18, 24, 32, 33, 34, 48, 49])
+def test_rows_begin_inside_long_occurrences(L):
+    """Rows of 16 bytes that begin inside long occurrences (runs of one
+    letter, planted copies of the longest patterns), so that a row's warm-up
+    must carry a deep state into it, for longest-pattern lengths on both
+    sides of multiples of the 16-byte word."""
+    rng = np.random.default_rng(1940 + L)
+    text = ACGT[rng.integers(0, 4, 60_000)]
+    text[1000:1400] = ord("A")                      # a run: deep states at many row starts
+    text[5003:5003 + 3 * L] = ord("C")
+    pats = [b"A" * L, b"C" * (L - 1), b"ACGT"]
+    pats += [text[o:o + L].tobytes() for o in rng.integers(0, text.size - L, 20)]
+    pats += [text[o:o + n].tobytes() for o, n in zip(rng.integers(0, text.size - L, 30), rng.integers(4, L, 30))]
+    text = workloads.embed(rng, text, pats[3:23], 400)
+    want = oracle.scan(pats, text)
+    a = A.ac_build(pats, alphabet="ACGT")
+    for threads in (64, 512, 1024):
+        A.ac_set_scan_config(a, kernel=A.AC_KERNEL_SHORT, row_len=16, threads=threads)
+        all_paths(a, text, want)
+    a16 = A.ac_build(pats, alphabet="ACGT", placement=A.AC_PLACE_HYBRID16, smem_table_bytes=256)
+    A.ac_set_scan_config(a16, kernel=A.AC_KERNEL_SHORT, row_len=16)
+    all_paths(a16, text, want)
 
 
 @pytest.mark.parametrize("config", ["config1", "config2"])
