@@ -1,4 +1,5 @@
-"""CUDA-graph capture of the asynchronous scan, as the first call of a process.
+"""CUDA-graph capture of the asynchronous scan, as the first call of a
+process, and stream order around its overlapped launches.
 
 A caller may capture ac_scan_async into a CUDA graph before it has ever
 called it. The library's one-time state (the stream-ordered scratch pool, the
@@ -82,3 +83,45 @@ def test_first_call_captured_in_a_graph(tmp_path):
             assert int(res[f"M{rep}_{i}"][0]) == wm.shape[0]
             assert np.array_equal(res[f"m{rep}_{i}"], wm)
             assert np.array_equal(res[f"c{rep}_{i}"], wc)
+
+
+def test_stream_order_around_overlapped_launches():
+    """ac_scan_async's scan and sort may start before the launch ahead of
+    them finishes (each waits for it before touching its results), so the
+    call must still see the text a kernel just before it wrote, and a kernel
+    just after it must see its results. Texts are written into one device
+    buffer by a copy kernel right before each call, and the results copied
+    out by kernels right after it, all on one stream with no synchronisation
+    in between; every call must equal the oracle for the text written
+    before it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1305_gb300 import ac as A
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(77)
+    w = workloads.config1()
+    a = A.ac_build(w.patterns, alphabet="ACGT")
+    texts = [w.text.copy()] + [workloads.embed(rng, w.text, w.patterns, 50 * (i + 1)) for i in range(5)]
+    srcs = [torch.from_numpy(t).cuda() for t in texts]
+    buf = torch.empty_like(srcs[0])
+    cap = 1 << 14
+    d_m = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
+    d_num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d_c = torch.zeros(a.num_patterns, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    outs = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for rep in range(3):
+            for src in srcs:
+                buf.copy_(src)
+                A.ac_scan_async(a, buf, buf.numel(), A.AC_U8, s, d_m, cap, d_num, d_c)
+                outs.append((d_num.clone(), d_m.clone(), d_c.clone()))
+    s.synchronize()
+    wants = [oracle.scan(w.patterns, t) for t in texts]
+    for k, (num, m, c) in enumerate(outs):
+        wm, wc = wants[k % len(texts)]
+        M = int(num.item())
+        assert M == wm.shape[0]
+        assert np.array_equal(m.view(-1, 2)[:M].cpu().numpy().view(np.uint32), wm)
+        assert np.array_equal(c.cpu().numpy(), wc)
