@@ -37,3 +37,16 @@ def test_refusals():
         with pytest.raises(A.AcError) as e:
             A.ac_probe_gather(0, **args)
         assert e.value.code == code, kw
+
+
+def test_launch_probe_in_a_graph():
+    """ac_probe_launch enqueues empty kernels that a CUDA graph captures,
+    one node each; replaying the graph runs them."""
+    s = torch.cuda.Stream()
+    A.ac_probe_launch(s, 3, 128, 512)  # outside a capture first
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        A.ac_probe_launch(torch.cuda.current_stream(), 6, 1, 32)
+    g.replay()
+    torch.cuda.synchronize()

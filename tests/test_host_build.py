@@ -150,6 +150,11 @@ def test_argument_errors():
     with pytest.raises(A.AcError) as e:
         A.ac_build([b"AC"], builder=9, device=-1)
     assert e.value.code == A.AC_EINVAL
+    # the launch probe refuses empty or oversized launches before touching a device
+    for args in ((0, 1, 32), (1, 0, 32), (1, 1, 0), (1, 1, 1025)):
+        with pytest.raises(A.AcError) as e:
+            A.ac_probe_launch(None, *args)
+        assert e.value.code == A.AC_EINVAL
 
 
 def test_explicit_alphabet_order_sets_symbol_codes():
