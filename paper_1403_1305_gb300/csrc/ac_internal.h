@@ -251,9 +251,12 @@ int launch_scan_batch(const BatchLaunch &b, const ScanOut &o, cudaStream_t strea
 int plan_smem(int device, const ac_scan_config &cfg, uint32_t sigma, int placement, uint32_t smem_cap,
               uint32_t max_states, uint32_t *rows_used, bool *hybrid, size_t *smem_bytes, uint32_t *table_words);
 int launch_fill_u64(unsigned long long *p, uint64_t count, unsigned long long value, cudaStream_t stream);
-// zero three ranges of 8-byte words (a pointer may be null when its count is 0) in one launch
+// zero three ranges of 8-byte words (a pointer may be null when its count is 0) in one launch;
+// overlap: it may start while the launch before it in the stream still runs (it waits for that
+// launch before writing; a scan launched overlapped behind it reads nothing written before the
+// call until it has finished)
 int launch_zero(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1, unsigned long long *p2,
-                uint64_t n2, cudaStream_t stream);
+                uint64_t n2, cudaStream_t stream, bool overlap = false);
 int launch_keys_to_matches(const unsigned long long *keys, const unsigned long long *num, uint64_t cap,
                            uint32_t shift, ac_match *out, unsigned long long *num_out, const uint32_t *err,
                            cudaStream_t stream);

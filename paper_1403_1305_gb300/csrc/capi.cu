@@ -1018,8 +1018,9 @@ static int scan_keys(const ac_automaton *a, const uint8_t *d_text, uint64_t n, i
         }
     }
     // error word, counter and counts zeroed by one launch
+    // (overlapped: it waits for the launch before it, whatever that is, before writing)
     rc = launch_zero((unsigned long long *)err, err ? 2 : 0, (unsigned long long *)d_num, 1,
-                     (unsigned long long *)d_counts, d_counts ? a->P : 0, s);
+                     (unsigned long long *)d_counts, d_counts ? a->P : 0, s, true);
     if (rc) return rc;
     if (n) {
         ScanText tx{t, n, fmt, readable};

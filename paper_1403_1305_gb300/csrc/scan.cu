@@ -47,6 +47,7 @@ __global__ void fill_u64_kernel(unsigned long long *p, uint64_t count, unsigned 
 __global__ void zero3_kernel(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1,
                              unsigned long long *p2, uint64_t n2) {
     kern::pdl_release();  // a scan or sort behind it may start; it waits for these writes
+    kern::pdl_wait();     // launched overlapped: the launch before it (which may read these words) is done
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n0 + n1 + n2; i += stride) {
         if (i < n0) p0[i] = 0;
@@ -854,12 +855,12 @@ int launch_fill_u64(unsigned long long *ptr, uint64_t count, unsigned long long 
 }
 
 int launch_zero(unsigned long long *p0, uint64_t n0, unsigned long long *p1, uint64_t n1, unsigned long long *p2,
-                uint64_t n2, cudaStream_t stream) {
+                uint64_t n2, cudaStream_t stream, bool overlap) {
     const uint64_t total = n0 + n1 + n2;
     if (!total) return AC_OK;
     const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 1024);
-    zero3_kernel<<<(unsigned)blocks, 256, 0, stream>>>(p0, n0, p1, n1, p2, n2);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_overlapped(zero3_kernel, dim3((unsigned)blocks), dim3(256), 0, stream, overlap, p0, n0, p1,
+                                      n1, p2, n2);
     return e == cudaSuccess ? AC_OK : set_error(AC_ECUDA, "zero: %s", cudaGetErrorString(e));
 }
 
@@ -910,7 +911,8 @@ __global__ void __launch_bounds__(kRankThreads)
                      uint32_t shift, ac_match *__restrict__ out, unsigned long long *num_out, const uint32_t *err) {
     extern __shared__ __align__(16) unsigned long long sk[];  // pairs(cap) * 2 keys
     __shared__ uint32_t part[kRankGroups][2][kRankPer];      // per group: each warp's counts
-    kern::pdl_wait();  // the keys, the counter and the error word of the launch before
+    kern::pdl_release();  // the next call's zeroing may start; it waits for this launch before writing
+    kern::pdl_wait();     // the keys, the counter and the error word of the launch before
     const uint32_t base = smem_addr(sk);
     const bool aligned = ((uintptr_t)keys & 15) == 0;
     // the first keys' copies go out with the count's read (copies past the

@@ -11,7 +11,7 @@
 // bytes at a time, so a launch costs one copy round trip per stage even when
 // rows are a few stages long. Here every thread loads its whole window
 // (warm-up words and row words, at most nine 16-byte words) straight into
-// registers with vector loads issued before the table is staged; a launch
+// registers with vector loads issued while the table is staged; a launch
 // is one memory round trip and one walk of (warm-up + row) symbols per
 // thread, and every warp of the grid walks at once.
 //
@@ -219,24 +219,6 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
     const int64_t nbytes = (int64_t)p.nbytes;
     const int64_t b0 = (int64_t)row * p.row_bytes - 16 * (int64_t)nw_warm;  // first byte of the window
 
-    // The window into registers; the loads stay in flight while the table is staged.
-    uint4 w[MAXW];
-#pragma unroll
-    for (int k = 0; k < MAXW; ++k) {
-        w[k] = make_uint4(0, 0, 0, 0);
-        const int64_t b = b0 + 16 * (int64_t)k;
-        if (active && (uint32_t)k < nw) {
-            if (b >= 0 && b + 16 <= nbytes) {
-                w[k] = __ldg(reinterpret_cast<const uint4 *>(p.text + b));  // 16-byte aligned
-            } else if (b + 16 > 0 && b < nbytes) {  // a text edge inside the word
-                uint32_t v[4] = {0, 0, 0, 0};
-                for (int j = 0; j < 16; ++j)
-                    if (b + j >= 0 && b + j < nbytes) v[j >> 2] |= (uint32_t)__ldg(p.text + b + j) << (8 * (j & 3));
-                w[k] = make_uint4(v[0], v[1], v[2], v[3]);
-            }
-        }
-    }
-
     // The table (and the symbol map) into shared memory.
     const uint32_t tbytes = (SM == SHORT_FULL) ? sd.states * 16u : p.smem_rows * 8u;
     uint8_t *tab = smem;
@@ -254,14 +236,34 @@ __global__ void __launch_bounds__(1024, 1) short_kernel(const __grid_constant__ 
             *reinterpret_cast<uint2 *>(tab + (tbytes & ~15u)) =
                 __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(src) + (tbytes & ~15u)));
         for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) smap[i] = p.sym_of_byte[i];
-        asm volatile("cp.async.wait_all;" ::: "memory");
     }
+    // The launch before this one (the zeroing of the counter and counts, which
+    // itself waited for everything before it) has finished from here on: the
+    // text, written before the call, may be read and the outputs written.
+    pdl_wait();
+
+    // The window into registers; the loads overlap the table's copies.
+    uint4 w[MAXW];
+#pragma unroll
+    for (int k = 0; k < MAXW; ++k) {
+        w[k] = make_uint4(0, 0, 0, 0);
+        const int64_t b = b0 + 16 * (int64_t)k;
+        if (active && (uint32_t)k < nw) {
+            if (b >= 0 && b + 16 <= nbytes) {
+                w[k] = __ldg(reinterpret_cast<const uint4 *>(p.text + b));  // 16-byte aligned
+            } else if (b + 16 > 0 && b < nbytes) {  // a text edge inside the word
+                uint32_t v[4] = {0, 0, 0, 0};
+                for (int j = 0; j < 16; ++j)
+                    if (b + j >= 0 && b + j < nbytes) v[j >> 2] |= (uint32_t)__ldg(p.text + b + j) << (8 * (j & 3));
+                w[k] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const uint32_t *ooff = sd.out_off;
     const uint32_t *oids = sd.out_ids;
-    // the counter, counts and keys are written below: the launch before this
-    // one (their zeroing) has finished by now
-    pdl_wait();
 
     // The walk, one word at a time (the window shifts down one word per
     // step): warm-up words from the root (positions before the text start
